@@ -1,0 +1,210 @@
+/*
+ * libsu3: the SU3_Bench link multiply on an NVIDIA GB300 (sm_103a), as a C ABI.
+ *
+ * The operation (arXiv 2103.00571, §Background "SU3_Bench"): for every site i of an L^4 lattice
+ * and each of its four links j, the 3x3 complex matrix a[i].link[j] is multiplied by the fixed
+ * per-direction 3x3 complex matrix b[j]:
+ *     c[i].link[j].e[k][l] = sum_{m=0..2} a[i].link[j].e[k][m] * b[j].e[m][l].
+ * Sites are independent; b is constant and shared by all sites (§Background, array sizes).
+ *
+ * Conventions shared by every entry point:
+ *  - Every call returns an su3_status; nothing throws, exits, aborts or traps on the device.
+ *    A failed call leaves a message that su3_last_error() returns.
+ *  - Pointers named *_dev are device (HBM) pointers owned by the caller and must be 16-byte
+ *    aligned. Pointers named *_host are host pointers owned by the caller.
+ *  - `stream` is a CUstream / cudaStream_t passed as void* (NULL = the legacy default stream).
+ *    Calls that take a stream only enqueue work on it and return without waiting; device-side
+ *    errors surface at su3_sync().
+ *  - b is always given on the host as FP64, double b[4][3][3][2] (link, row, column, re/im),
+ *    and copied at call time, so the caller may free or change it as soon as the call returns.
+ *  - A handle is not thread-safe: use one handle per host thread.
+ */
+#ifndef SU3_H
+#define SU3_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define SU3_ABI_VERSION 1
+
+typedef enum {
+  SU3_OK = 0,
+  SU3_ERR_INVALID_ARG = 1,      /* null/misaligned pointer, bad size, stride, overlap, enum */
+  SU3_ERR_UNSUPPORTED = 2,      /* a valid but unimplemented combination of forms */
+  SU3_ERR_CUDA = 3,             /* a CUDA runtime call failed (message says which) */
+  SU3_ERR_NOT_INITIALIZED = 4,  /* null handle */
+  SU3_ERR_TIMEOUT = 5,          /* a bounded wait ran out (host deadline or device mbarrier) */
+  SU3_ERR_FAULT_INJECTED = 6    /* SU3_FAULT_INJECT made this call fail on the host */
+} su3_status;
+
+/* Storage type of the real numbers. F64 computes in FP64; F32/F16/BF16 compute in FP32. */
+typedef enum { SU3_F64 = 0, SU3_F32 = 1, SU3_F16 = 2, SU3_BF16 = 3 } su3_dtype;
+
+/*
+ * Representation of one link matrix. FULL18: 9 complex numbers, row major. TWOROW12: rows 0
+ * and 1 only (6 complex numbers); row 2 of an SU(3) matrix is conj(row0 x row1) and is rebuilt
+ * on the fly. (The paper stores all 18 reals; the two-row form is the MILC-style compression.)
+ */
+typedef enum { SU3_REPR_FULL18 = 0, SU3_REPR_TWOROW12 = 1 } su3_repr;
+
+/*
+ * Memory layout of an array of links. A "complex element" is (re, im) adjacent in memory.
+ * Link q = 4*i + j is link j of site i; e indexes the complex elements of a link (0..8 or 0..5).
+ *  AOS:     the paper's Site array (§Background, the Site structure): site i starts at byte
+ *           i*site_stride_bytes, link j at +j*link_bytes, element e at +e*2*sizeof(real).
+ *           Bytes of a site past its 4 links (the paper's coordinates/index/parity/pad) are
+ *           never read by a kernel as data and never written.
+ *  AOSOA32: blocks of 32 links; element e of link q at complex index
+ *           ((q/32)*n_elem + e)*32 + q%32. The last block is padded to 32 links.
+ *  SOA:     element e of link q at complex index e*n_links + q.
+ */
+typedef enum { SU3_LAYOUT_AOS = 0, SU3_LAYOUT_AOSOA32 = 1, SU3_LAYOUT_SOA = 2 } su3_layout;
+
+/*
+ * Arithmetic of the F64 storage type. NATIVE: FP64 fused multiply-adds (the plain method).
+ * F32PAIR: FP64 storage, products and sums carried as unevaluated pairs of FP32 numbers
+ * (error-free TwoProd/TwoSum transformations); accurate to about 2^-46 relative to the largest
+ * product for |values| < 2^60, and far faster on GB300, whose FP64 units are 1/64 of its FP32
+ * rate. Ignored (must be NATIVE) for F32/F16/BF16 storage.
+ */
+typedef enum { SU3_ARITH_NATIVE = 0, SU3_ARITH_F32PAIR = 1 } su3_arith;
+
+typedef struct {
+  int32_t dtype;              /* su3_dtype */
+  int32_t repr;               /* su3_repr */
+  int32_t layout;             /* su3_layout */
+  int32_t arith;              /* su3_arith */
+  int64_t n_sites;            /* number of sites (4 links each); 0 is a valid no-op */
+  int64_t site_stride_bytes;  /* AOS only: bytes between sites; 0 = packed (4*link bytes);
+                                 otherwise >= 4*link bytes and a multiple of 16 */
+} su3_desc;
+
+typedef struct su3_handle su3_handle;
+
+/* Launch configuration of the streaming kernels (for the autotuner); 0 fields = default. */
+typedef struct {
+  int32_t block;        /* threads per CTA (multiple of 32, <= 1024) */
+  int32_t tile_sites;   /* AOS: sites per shared-memory tile; others: links per thread x 32 */
+  int32_t stages;       /* AOS: shared-memory pipeline depth (2..8) */
+  int32_t ctas_per_sm;  /* CTAs per SM in the persistent grid */
+} su3_launch_cfg;
+
+/* One lattice of a batched call. a/c are device pointers; b as in su3_mult. */
+typedef struct {
+  su3_desc desc;     /* dtype F64 or F32, FULL18, AOS packed, arith NATIVE */
+  const void* a_dev;
+  void* c_dev;
+  double b[4][3][3][2];
+} su3_batch_item;
+
+/* ---- lifetime ---------------------------------------------------------------------------- */
+
+/* Binds a new handle to CUDA device `device` (which becomes current on this thread). The
+ * handle owns a small status word in device memory and the batched workspace. */
+su3_status su3_init(int device, su3_handle** out);
+
+/* Releases everything the handle owns (after synchronising its device). NULL is a no-op. */
+su3_status su3_finalize(su3_handle* h);
+
+/* ---- the operation ----------------------------------------------------------------------- */
+
+/*
+ * c = a x b[j] for every link (the SU3_Bench kernel, §Background). `a_desc` describes a_dev and
+ * `c_desc` describes c_dev (NULL = same as a_desc). Both must have the same dtype, layout,
+ * arith and n_sites. Supported repr pairs (a -> c): FULL18 -> FULL18, TWOROW12 -> TWOROW12
+ * (rows 0-1 of c only), TWOROW12 -> FULL18 (row 2 of a rebuilt in registers).
+ * a_dev == c_dev (exactly in place, same desc) is allowed; any other overlap is INVALID_ARG.
+ * For F16/BF16/F32 storage, b is rounded once to FP32; results are rounded once to storage.
+ * Asynchronous on `stream`.
+ */
+su3_status su3_mult(su3_handle* h, const su3_desc* a_desc, const void* a_dev,
+                    const double* b, const su3_desc* c_desc, void* c_dev, void* stream);
+
+/*
+ * The same operation with HOST buffers: a_host is copied to the device in chunks, multiplied
+ * and copied back into c_host, with copies and kernels overlapped on the handle's streams.
+ * Synchronous: returns when c_host is complete. Pinned host memory (cudaHostRegister or
+ * cudaMallocHost) gives full NVLink-C2C speed; pageable memory works but is slower.
+ * Allocates (once, then reuses) device staging buffers owned by the handle.
+ */
+su3_status su3_mult_host(su3_handle* h, const su3_desc* a_desc, const void* a_host,
+                         const double* b, const su3_desc* c_desc, void* c_host, void* stream);
+
+/*
+ * Many independent lattices (each its own a, b, c, n_sites and storage type) in ONE persistent
+ * kernel launch: the link tiles of all lattices form one global work list that the CTAs
+ * stride over. With use_graph != 0 the launch (descriptor upload + kernel) is captured once into
+ * a CUDA graph keyed by the item list and replayed with cudaGraphLaunch on later identical calls.
+ * Supported items: dtype F64 or F32, FULL18, AOS packed, NATIVE. The item array is copied at
+ * call time into handle-owned device memory (the handle's workspace).
+ */
+su3_status su3_mult_batched(su3_handle* h, int32_t n, const su3_batch_item* items, void* stream,
+                            int32_t use_graph);
+
+/* ---- layout and precision conversion (outside the timed path) --------------------------- */
+
+/*
+ * Converts packed FP64 AOS sites (72 doubles each, the benchmark's input format) into the form
+ * `dst` describes: each real rounded once, to nearest even, straight from FP64; TWOROW12 drops
+ * row 2. dst->n_sites sites are converted.
+ */
+su3_status su3_pack(su3_handle* h, const double* aos_f64_dev, const su3_desc* dst, void* dst_dev,
+                    void* stream);
+
+/*
+ * Converts an array in the form `src` describes back to packed FP64 AOS sites (exact widening;
+ * TWOROW12 gets row 2 rebuilt as conj(row0 x row1) in FP64).
+ */
+su3_status su3_unpack(su3_handle* h, const su3_desc* src, const void* src_dev, double* aos_f64_dev,
+                      void* stream);
+
+/* ---- completion, errors, sizes, tuning --------------------------------------------------- */
+
+/*
+ * Waits for all work enqueued on `stream` (timeout_ms < 0: no host deadline; otherwise polls
+ * until the deadline and returns SU3_ERR_TIMEOUT if the work is still running). Then reads and
+ * clears the handle's device status word: a device-side bounded wait that ran out is reported
+ * as SU3_ERR_TIMEOUT, an asynchronous CUDA error as SU3_ERR_CUDA.
+ */
+su3_status su3_sync(su3_handle* h, void* stream, int32_t timeout_ms);
+
+const char* su3_status_string(su3_status s);
+const char* su3_last_error(const su3_handle* h);
+
+/* Bytes of one link (18 or 12 reals of the dtype) and bytes an array of `d` occupies. */
+int64_t su3_link_bytes(int32_t dtype, int32_t repr);
+int64_t su3_array_bytes(const su3_desc* d);
+
+/* Validates a descriptor without touching the GPU (returns INVALID_ARG/UNSUPPORTED/OK). */
+su3_status su3_check_desc(const su3_desc* d);
+
+/* Per-form launch configuration used by su3_mult (the autotuner writes it). */
+su3_status su3_set_launch_cfg(su3_handle* h, const su3_desc* form, const su3_launch_cfg* cfg);
+su3_status su3_get_launch_cfg(su3_handle* h, const su3_desc* form, su3_launch_cfg* cfg);
+
+/* Launch configuration of su3_mult_batched (tile_sites = sites per work tile; the cached graph
+ * is rebuilt on the next graph-mode call). 0 fields keep the current value. */
+su3_status su3_set_batched_cfg(su3_handle* h, const su3_launch_cfg* cfg);
+su3_status su3_get_batched_cfg(su3_handle* h, su3_launch_cfg* cfg);
+
+/* Number of kernel launches this handle has made since su3_init (for launch accounting). */
+int64_t su3_launch_count(const su3_handle* h);
+
+/*
+ * Failure-path self test (not part of the operation): launches one CTA that waits, through the
+ * same bounded mbarrier wait every streaming kernel uses, on a barrier that nothing completes,
+ * with a limit of `limit_ms` (1..2000) instead of the kernels' 4 s. The kernel then records a
+ * timeout in the handle's status word and returns, so a following su3_sync() must report
+ * SU3_ERR_TIMEOUT while the CUDA context stays usable.
+ */
+su3_status su3_selftest_wait_timeout(su3_handle* h, int32_t limit_ms, void* stream);
+
+int32_t su3_abi_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SU3_H */

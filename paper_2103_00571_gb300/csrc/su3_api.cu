@@ -1,0 +1,639 @@
+// libsu3 C ABI: handle, argument validation, dispatch, completion and error reporting, the
+// host-buffer path and the batched/graph path. The operation itself is the SU3_Bench link multiply
+// (arXiv 2103.00571, §Background "SU3_Bench"); the kernels live in su3_stream.cu,
+// su3_batched.cu and su3_pack.cu.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <stdlib.h>
+#include <string.h>
+
+#include <algorithm>
+#include <chrono>
+#include <map>
+#include <string>
+#include <thread>
+#include <tuple>
+#include <vector>
+
+#include "su3.h"
+#include "su3_internal.h"
+
+using namespace su3;
+
+namespace {
+
+enum FaultPoint { kFaultNone = 0, kFaultLaunch = 1, kFaultAlloc = 2, kFaultCopy = 4, kFaultSync = 8 };
+
+int parse_fault_env() {
+  const char* v = getenv("SU3_FAULT_INJECT");
+  if (!v) return kFaultNone;
+  int f = 0;
+  std::string s(v);
+  if (s.find("launch") != std::string::npos) f |= kFaultLaunch;
+  if (s.find("alloc") != std::string::npos) f |= kFaultAlloc;
+  if (s.find("copy") != std::string::npos) f |= kFaultCopy;
+  if (s.find("sync") != std::string::npos) f |= kFaultSync;
+  return f;
+}
+
+constexpr int kHostBuffers = 3;
+
+}  // namespace
+
+struct su3_handle {
+  int device = 0;
+  int num_sms = 0;
+  unsigned* status_dev = nullptr;
+  int64_t launches = 0;
+  std::string err;
+  int fault = 0;
+  std::map<std::tuple<int, int, int, int, int>, LaunchCfg> cfgs;
+  // batched, direct mode
+  BatchDesc* bdesc_dev = nullptr;
+  BatchDesc* bdesc_host = nullptr;  // pinned
+  int bcap = 0;
+  cudaEvent_t bcopy_done = nullptr;
+  bool bcopy_pending = false;
+  // batched, graph mode (its own descriptor buffers: a replay re-reads them)
+  BatchDesc* gdesc_dev = nullptr;
+  BatchDesc* gdesc_host = nullptr;
+  int gcap = 0;
+  cudaGraphExec_t gexec = nullptr;
+  std::vector<char> gkey;
+  cudaStream_t cap_stream = nullptr;
+  BatchCfg bcfg;
+  // host-buffer path
+  unsigned char* hbuf_dev[kHostBuffers] = {nullptr, nullptr, nullptr};
+  size_t hbuf_bytes = 0;
+  cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
+  cudaEvent_t ev_h2d[kHostBuffers] = {}, ev_comp[kHostBuffers] = {}, ev_d2h[kHostBuffers] = {};
+  cudaEvent_t ev_start = nullptr;
+};
+
+namespace {
+
+su3_status fail(su3_handle* h, su3_status s, const std::string& msg) {
+  if (h) h->err = msg;
+  return s;
+}
+
+su3_status cuda_err(su3_handle* h, const char* what, cudaError_t e) {
+  return fail(h, SU3_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15u) == 0; }
+
+LaunchCtx ctx_of(su3_handle* h, cudaStream_t st) {
+  LaunchCtx c;
+  c.stream = st;
+  c.status = h->status_dev;
+  c.num_sms = h->num_sms;
+  c.launches = &h->launches;
+  c.err = &h->err;
+  return c;
+}
+
+std::tuple<int, int, int, int, int> form_key(const su3_desc* d) {
+  return std::make_tuple((int)d->dtype, (int)d->repr, (int)d->layout, (int)d->arith, 0);
+}
+
+int64_t resolved_stride(const su3_desc* d) {
+  if (d->layout != SU3_LAYOUT_AOS) return 0;
+  return d->site_stride_bytes ? d->site_stride_bytes : 4 * link_bytes(d->dtype, d->repr);
+}
+
+su3_status check_cfg(su3_handle* h, const Form& f, const LaunchCfg& c) {
+  if (c.block < 32 || c.block > 256 || c.block % 32)
+    return fail(h, SU3_ERR_INVALID_ARG, "block must be a multiple of 32 in [32, 256]");
+  if (c.ctas_per_sm < 1 || c.ctas_per_sm > 32) return fail(h, SU3_ERR_INVALID_ARG, "ctas_per_sm must be in [1, 32]");
+  if (f.layout == SU3_LAYOUT_AOS) {
+    if (c.stages < 2 || c.stages > 8) return fail(h, SU3_ERR_INVALID_ARG, "stages must be in [2, 8]");
+    if (c.tile_sites < 1 || c.tile_sites > 1024) return fail(h, SU3_ERR_INVALID_ARG, "tile_sites must be in [1, 1024]");
+    if ((int64_t)c.tile_sites * f.a_stride > (1 << 20))
+      return fail(h, SU3_ERR_INVALID_ARG, "a tile may not exceed 1 MiB");
+  } else if (c.tile_sites != 1 && c.tile_sites != 2 && c.tile_sites != 4) {
+    return fail(h, SU3_ERR_INVALID_ARG, "links per thread (tile_sites) must be 1, 2 or 4 for SOA/AOSOA32");
+  }
+  return SU3_OK;
+}
+
+LaunchCfg cfg_for(su3_handle* h, const su3_desc* d, const Form& f) {
+  auto it = h->cfgs.find(form_key(d));
+  if (it != h->cfgs.end()) return it->second;
+  return default_cfg(f);
+}
+
+// Validates an (a, c) descriptor pair into a Form.
+su3_status make_form(su3_handle* h, const su3_desc* ad, const su3_desc* cd, Form* f) {
+  su3_status s = su3_check_desc(ad);
+  if (s != SU3_OK) return fail(h, s, "invalid a descriptor (dtype/repr/layout/arith/n_sites/stride)");
+  s = su3_check_desc(cd);
+  if (s != SU3_OK) return fail(h, s, "invalid c descriptor (dtype/repr/layout/arith/n_sites/stride)");
+  if (ad->dtype != cd->dtype || ad->layout != cd->layout || ad->arith != cd->arith || ad->n_sites != cd->n_sites)
+    return fail(h, SU3_ERR_INVALID_ARG, "a and c must share dtype, layout, arith and n_sites");
+  if (ad->repr == SU3_REPR_FULL18 && cd->repr != SU3_REPR_FULL18)
+    return fail(h, SU3_ERR_UNSUPPORTED, "FULL18 input needs FULL18 output");
+  if (ad->arith != SU3_ARITH_NATIVE)
+    return fail(h, SU3_ERR_UNSUPPORTED, "F32PAIR arithmetic is not available in this build");
+  f->dtype = ad->dtype;
+  f->repr_in = ad->repr;
+  f->repr_out = cd->repr;
+  f->layout = ad->layout;
+  f->arith = ad->arith;
+  f->n_sites = ad->n_sites;
+  f->a_stride = resolved_stride(ad);
+  f->c_stride = resolved_stride(cd);
+  return SU3_OK;
+}
+
+bool ranges_overlap(const void* a, int64_t an, const void* b, int64_t bn) {
+  const uintptr_t a0 = (uintptr_t)a, b0 = (uintptr_t)b;
+  return a0 < b0 + (uintptr_t)bn && b0 < a0 + (uintptr_t)an;
+}
+
+}  // namespace
+
+extern "C" {
+
+int32_t su3_abi_version(void) { return SU3_ABI_VERSION; }
+
+const char* su3_status_string(su3_status s) {
+  switch (s) {
+    case SU3_OK: return "SU3_OK";
+    case SU3_ERR_INVALID_ARG: return "SU3_ERR_INVALID_ARG";
+    case SU3_ERR_UNSUPPORTED: return "SU3_ERR_UNSUPPORTED";
+    case SU3_ERR_CUDA: return "SU3_ERR_CUDA";
+    case SU3_ERR_NOT_INITIALIZED: return "SU3_ERR_NOT_INITIALIZED";
+    case SU3_ERR_TIMEOUT: return "SU3_ERR_TIMEOUT";
+    case SU3_ERR_FAULT_INJECTED: return "SU3_ERR_FAULT_INJECTED";
+  }
+  return "SU3_ERR_UNKNOWN";
+}
+
+const char* su3_last_error(const su3_handle* h) { return h ? h->err.c_str() : "null handle"; }
+
+int64_t su3_launch_count(const su3_handle* h) { return h ? h->launches : 0; }
+
+int64_t su3_link_bytes(int32_t dtype, int32_t repr) {
+  if (dtype < SU3_F64 || dtype > SU3_BF16 || repr < SU3_REPR_FULL18 || repr > SU3_REPR_TWOROW12) return 0;
+  return link_bytes(dtype, repr);
+}
+
+su3_status su3_check_desc(const su3_desc* d) {
+  if (!d) return SU3_ERR_INVALID_ARG;
+  if (d->dtype < SU3_F64 || d->dtype > SU3_BF16) return SU3_ERR_INVALID_ARG;
+  if (d->repr < SU3_REPR_FULL18 || d->repr > SU3_REPR_TWOROW12) return SU3_ERR_INVALID_ARG;
+  if (d->layout < SU3_LAYOUT_AOS || d->layout > SU3_LAYOUT_SOA) return SU3_ERR_INVALID_ARG;
+  if (d->arith < SU3_ARITH_NATIVE || d->arith > SU3_ARITH_F32PAIR) return SU3_ERR_INVALID_ARG;
+  if (d->arith == SU3_ARITH_F32PAIR && d->dtype != SU3_F64) return SU3_ERR_INVALID_ARG;
+  if (d->n_sites < 0 || d->n_sites > ((int64_t)1 << 36)) return SU3_ERR_INVALID_ARG;
+  const int64_t lb = link_bytes(d->dtype, d->repr);
+  if (d->layout == SU3_LAYOUT_AOS) {
+    if (d->site_stride_bytes != 0 && (d->site_stride_bytes < 4 * lb || d->site_stride_bytes % 16 != 0))
+      return SU3_ERR_INVALID_ARG;
+  } else if (d->site_stride_bytes != 0) {
+    return SU3_ERR_INVALID_ARG;
+  }
+  return SU3_OK;
+}
+
+int64_t su3_array_bytes(const su3_desc* d) {
+  if (su3_check_desc(d) != SU3_OK) return -1;
+  const int64_t lb = link_bytes(d->dtype, d->repr);
+  switch (d->layout) {
+    case SU3_LAYOUT_AOS: return d->n_sites * resolved_stride(d);
+    case SU3_LAYOUT_SOA: return 4 * d->n_sites * lb;
+    case SU3_LAYOUT_AOSOA32: return (4 * d->n_sites + 31) / 32 * 32 * lb;
+  }
+  return -1;
+}
+
+su3_status su3_init(int device, su3_handle** out) {
+  if (!out) return SU3_ERR_INVALID_ARG;
+  *out = nullptr;
+  su3_handle* h = new su3_handle();
+  h->fault = parse_fault_env();
+  h->device = device;
+  h->bcfg = default_batch_cfg();
+  if (h->fault & kFaultAlloc) {
+    delete h;
+    return SU3_ERR_FAULT_INJECTED;
+  }
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess) e = cudaMalloc((void**)&h->status_dev, sizeof(unsigned));
+  if (e == cudaSuccess) e = cudaMemset(h->status_dev, 0, sizeof(unsigned));
+  if (e != cudaSuccess) {
+    if (h->status_dev) cudaFree(h->status_dev);
+    delete h;
+    return SU3_ERR_CUDA;
+  }
+  *out = h;
+  return SU3_OK;
+}
+
+su3_status su3_finalize(su3_handle* h) {
+  if (!h) return SU3_OK;
+  cudaSetDevice(h->device);
+  cudaDeviceSynchronize();
+  if (h->gexec) cudaGraphExecDestroy(h->gexec);
+  if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
+  cudaFree(h->bdesc_dev);
+  cudaFreeHost(h->bdesc_host);
+  cudaFree(h->gdesc_dev);
+  cudaFreeHost(h->gdesc_host);
+  if (h->bcopy_done) cudaEventDestroy(h->bcopy_done);
+  for (int i = 0; i < kHostBuffers; ++i) {
+    cudaFree(h->hbuf_dev[i]);
+    if (h->ev_h2d[i]) cudaEventDestroy(h->ev_h2d[i]);
+    if (h->ev_comp[i]) cudaEventDestroy(h->ev_comp[i]);
+    if (h->ev_d2h[i]) cudaEventDestroy(h->ev_d2h[i]);
+  }
+  if (h->ev_start) cudaEventDestroy(h->ev_start);
+  if (h->s_h2d) cudaStreamDestroy(h->s_h2d);
+  if (h->s_comp) cudaStreamDestroy(h->s_comp);
+  if (h->s_d2h) cudaStreamDestroy(h->s_d2h);
+  cudaFree(h->status_dev);
+  delete h;
+  return SU3_OK;
+}
+
+su3_status su3_set_launch_cfg(su3_handle* h, const su3_desc* form, const su3_launch_cfg* cfg) {
+  if (!h) return SU3_ERR_NOT_INITIALIZED;
+  if (!form || !cfg) return fail(h, SU3_ERR_INVALID_ARG, "null form or cfg");
+  if (su3_check_desc(form) != SU3_OK) return fail(h, SU3_ERR_INVALID_ARG, "invalid form descriptor");
+  Form f{};
+  f.dtype = form->dtype;
+  f.repr_in = f.repr_out = form->repr;
+  f.layout = form->layout;
+  f.arith = form->arith;
+  f.n_sites = form->n_sites;
+  f.a_stride = f.c_stride = resolved_stride(form);
+  LaunchCfg c = default_cfg(f);
+  if (cfg->block) c.block = cfg->block;
+  if (cfg->tile_sites) c.tile_sites = cfg->tile_sites;
+  if (cfg->stages) c.stages = cfg->stages;
+  if (cfg->ctas_per_sm) c.ctas_per_sm = cfg->ctas_per_sm;
+  su3_status s = check_cfg(h, f, c);
+  if (s != SU3_OK) return s;
+  h->cfgs[form_key(form)] = c;
+  return SU3_OK;
+}
+
+su3_status su3_get_launch_cfg(su3_handle* h, const su3_desc* form, su3_launch_cfg* cfg) {
+  if (!h) return SU3_ERR_NOT_INITIALIZED;
+  if (!form || !cfg || su3_check_desc(form) != SU3_OK) return fail(h, SU3_ERR_INVALID_ARG, "invalid form or cfg");
+  Form f{};
+  f.dtype = form->dtype;
+  f.repr_in = f.repr_out = form->repr;
+  f.layout = form->layout;
+  f.n_sites = form->n_sites;
+  f.a_stride = f.c_stride = resolved_stride(form);
+  LaunchCfg c = cfg_for(h, form, f);
+  cfg->block = c.block;
+  cfg->tile_sites = c.tile_sites;
+  cfg->stages = c.stages;
+  cfg->ctas_per_sm = c.ctas_per_sm;
+  return SU3_OK;
+}
+
+su3_status su3_set_batched_cfg(su3_handle* h, const su3_launch_cfg* cfg) {
+  if (!h) return SU3_ERR_NOT_INITIALIZED;
+  if (!cfg) return fail(h, SU3_ERR_INVALID_ARG, "null cfg");
+  BatchCfg c = h->bcfg;
+  if (cfg->block) c.block = cfg->block;
+  if (cfg->tile_sites) c.tile_sites = cfg->tile_sites;
+  if (cfg->stages) c.stages = cfg->stages;
+  if (cfg->ctas_per_sm) c.ctas_per_sm = cfg->ctas_per_sm;
+  if (c.block < 32 || c.block > 256 || c.block % 32 || c.stages < 2 || c.stages > 8 || c.tile_sites < 1 ||
+      c.tile_sites > 256 || c.ctas_per_sm < 1 || c.ctas_per_sm > 32)
+    return fail(h, SU3_ERR_INVALID_ARG, "batched cfg out of range (block 32..256 step 32, stages 2..8, "
+                                        "tile_sites 1..256, ctas_per_sm 1..32)");
+  h->bcfg = c;
+  h->gkey.clear();  // the next graph-mode call captures a new graph
+  return SU3_OK;
+}
+
+su3_status su3_get_batched_cfg(su3_handle* h, su3_launch_cfg* cfg) {
+  if (!h) return SU3_ERR_NOT_INITIALIZED;
+  if (!cfg) return fail(h, SU3_ERR_INVALID_ARG, "null cfg");
+  cfg->block = h->bcfg.block;
+  cfg->tile_sites = h->bcfg.tile_sites;
+  cfg->stages = h->bcfg.stages;
+  cfg->ctas_per_sm = h->bcfg.ctas_per_sm;
+  return SU3_OK;
+}
+
+su3_status su3_mult(su3_handle* h, const su3_desc* a_desc, const void* a_dev, const double* b,
+                    const su3_desc* c_desc, void* c_dev, void* stream) {
+  if (!h) return SU3_ERR_NOT_INITIALIZED;
+  if (!a_desc || !b) return fail(h, SU3_ERR_INVALID_ARG, "null descriptor or b");
+  if (!c_desc) c_desc = a_desc;
+  Form f;
+  su3_status s = make_form(h, a_desc, c_desc, &f);
+  if (s != SU3_OK) return s;
+  if (f.n_sites == 0) return SU3_OK;
+  if (!a_dev || !c_dev) return fail(h, SU3_ERR_INVALID_ARG, "null a or c");
+  if (!aligned16(a_dev) || !aligned16(c_dev)) return fail(h, SU3_ERR_INVALID_ARG, "a and c must be 16-byte aligned");
+  const int64_t an = su3_array_bytes(a_desc), cn = su3_array_bytes(c_desc);
+  if (a_dev == c_dev) {
+    if (a_desc->repr != c_desc->repr || f.a_stride != f.c_stride)
+      return fail(h, SU3_ERR_INVALID_ARG, "in-place operation needs identical a and c descriptors");
+  } else if (ranges_overlap(a_dev, an, c_dev, cn)) {
+    return fail(h, SU3_ERR_INVALID_ARG, "a and c overlap without being the same array");
+  }
+  if (h->fault & kFaultLaunch) return fail(h, SU3_ERR_FAULT_INJECTED, "fault injected at launch");
+  LaunchCfg cfg = cfg_for(h, a_desc, f);
+  s = check_cfg(h, f, cfg);
+  if (s != SU3_OK) return s;
+  return launch_mult(f, cfg, a_dev, b, c_dev, ctx_of(h, (cudaStream_t)stream));
+}
+
+su3_status su3_pack(su3_handle* h, const double* src, const su3_desc* dst, void* dst_dev, void* stream) {
+  if (!h) return SU3_ERR_NOT_INITIALIZED;
+  if (!dst || su3_check_desc(dst) != SU3_OK) return fail(h, SU3_ERR_INVALID_ARG, "invalid destination descriptor");
+  if (dst->n_sites == 0) return SU3_OK;
+  if (!src || !dst_dev || !aligned16(src) || !aligned16(dst_dev))
+    return fail(h, SU3_ERR_INVALID_ARG, "null or misaligned pointer");
+  if (ranges_overlap(src, dst->n_sites * 576, dst_dev, su3_array_bytes(dst)))
+    return fail(h, SU3_ERR_INVALID_ARG, "source and destination overlap");
+  if (h->fault & kFaultLaunch) return fail(h, SU3_ERR_FAULT_INJECTED, "fault injected at launch");
+  Form f{};
+  f.dtype = dst->dtype;
+  f.repr_in = f.repr_out = dst->repr;
+  f.layout = dst->layout;
+  f.n_sites = dst->n_sites;
+  f.a_stride = f.c_stride = resolved_stride(dst);
+  return launch_pack(f, src, dst_dev, ctx_of(h, (cudaStream_t)stream));
+}
+
+su3_status su3_unpack(su3_handle* h, const su3_desc* src, const void* src_dev, double* dst, void* stream) {
+  if (!h) return SU3_ERR_NOT_INITIALIZED;
+  if (!src || su3_check_desc(src) != SU3_OK) return fail(h, SU3_ERR_INVALID_ARG, "invalid source descriptor");
+  if (src->n_sites == 0) return SU3_OK;
+  if (!src_dev || !dst || !aligned16(src_dev) || !aligned16(dst))
+    return fail(h, SU3_ERR_INVALID_ARG, "null or misaligned pointer");
+  if (ranges_overlap(dst, src->n_sites * 576, src_dev, su3_array_bytes(src)))
+    return fail(h, SU3_ERR_INVALID_ARG, "source and destination overlap");
+  if (h->fault & kFaultLaunch) return fail(h, SU3_ERR_FAULT_INJECTED, "fault injected at launch");
+  Form f{};
+  f.dtype = src->dtype;
+  f.repr_in = f.repr_out = src->repr;
+  f.layout = src->layout;
+  f.n_sites = src->n_sites;
+  f.a_stride = f.c_stride = resolved_stride(src);
+  return launch_unpack(f, src_dev, dst, ctx_of(h, (cudaStream_t)stream));
+}
+
+su3_status su3_sync(su3_handle* h, void* stream, int32_t timeout_ms) {
+  if (!h) return SU3_ERR_NOT_INITIALIZED;
+  if (h->fault & kFaultSync) return fail(h, SU3_ERR_FAULT_INJECTED, "fault injected at sync");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  if (timeout_ms < 0) {
+    e = cudaStreamSynchronize(st);
+  } else {
+    const auto deadline = std::chrono::steady_clock::now() + std::chrono::milliseconds(timeout_ms);
+    for (;;) {
+      e = cudaStreamQuery(st);
+      if (e != cudaErrorNotReady) break;
+      if (std::chrono::steady_clock::now() > deadline)
+        return fail(h, SU3_ERR_TIMEOUT, "work on the stream did not finish within the host deadline");
+      std::this_thread::sleep_for(std::chrono::microseconds(50));
+    }
+  }
+  if (e != cudaSuccess) return cuda_err(h, "asynchronous CUDA error", e);
+  unsigned st_word = 0;
+  e = cudaMemcpy(&st_word, h->status_dev, sizeof(unsigned), cudaMemcpyDeviceToHost);
+  if (e != cudaSuccess) return cuda_err(h, "reading the device status word", e);
+  if (st_word) {
+    cudaMemset(h->status_dev, 0, sizeof(unsigned));
+    if (st_word & kDevErrTimeout)
+      return fail(h, SU3_ERR_TIMEOUT, "a device-side bounded wait (mbarrier) ran out; results are incomplete");
+    return fail(h, SU3_ERR_CUDA, "device status word reported an error");
+  }
+  return SU3_OK;
+}
+
+su3_status su3_selftest_wait_timeout(su3_handle* h, int32_t limit_ms, void* stream) {
+  if (!h) return SU3_ERR_NOT_INITIALIZED;
+  if (limit_ms < 1 || limit_ms > 2000) return fail(h, SU3_ERR_INVALID_ARG, "limit_ms must be in [1, 2000]");
+  return launch_selftest_wait(limit_ms, ctx_of(h, (cudaStream_t)stream));
+}
+
+// ---- host-buffer path ---------------------------------------------------------------------------
+
+su3_status su3_mult_host(su3_handle* h, const su3_desc* a_desc, const void* a_host, const double* b,
+                         const su3_desc* c_desc, void* c_host, void* stream) {
+  if (!h) return SU3_ERR_NOT_INITIALIZED;
+  if (!a_desc || !b) return fail(h, SU3_ERR_INVALID_ARG, "null descriptor or b");
+  if (!c_desc) c_desc = a_desc;
+  Form f;
+  su3_status s = make_form(h, a_desc, c_desc, &f);
+  if (s != SU3_OK) return s;
+  if (f.n_sites == 0) return SU3_OK;
+  if (f.layout != SU3_LAYOUT_AOS)
+    return fail(h, SU3_ERR_UNSUPPORTED, "the host-buffer path takes AOS arrays (chunks are whole sites)");
+  if (!a_host || !c_host) return fail(h, SU3_ERR_INVALID_ARG, "null a or c");
+  if (a_host != c_host && ranges_overlap(a_host, su3_array_bytes(a_desc), c_host, su3_array_bytes(c_desc)))
+    return fail(h, SU3_ERR_INVALID_ARG, "a and c overlap without being the same array");
+  if (h->fault & kFaultCopy) return fail(h, SU3_ERR_FAULT_INJECTED, "fault injected at copy");
+  LaunchCfg cfg = cfg_for(h, a_desc, f);
+  s = check_cfg(h, f, cfg);
+  if (s != SU3_OK) return s;
+  cudaError_t e;
+  if (!h->s_h2d) {
+    for (cudaStream_t* p : {&h->s_h2d, &h->s_comp, &h->s_d2h}) {
+      e = cudaStreamCreateWithFlags(p, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return cuda_err(h, "cudaStreamCreate", e);
+    }
+    for (int i = 0; i < kHostBuffers; ++i) {
+      for (cudaEvent_t* p : {&h->ev_h2d[i], &h->ev_comp[i], &h->ev_d2h[i]}) {
+        e = cudaEventCreateWithFlags(p, cudaEventDisableTiming);
+        if (e != cudaSuccess) return cuda_err(h, "cudaEventCreate", e);
+      }
+    }
+    e = cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming);
+    if (e != cudaSuccess) return cuda_err(h, "cudaEventCreate", e);
+  }
+  // chunks of whole sites, a multiple of the kernel tile, ~64 MB of input each
+  const int64_t a_site = f.a_stride, c_site = f.c_stride;
+  int64_t chunk = std::max<int64_t>(cfg.tile_sites, (64ll << 20) / a_site / cfg.tile_sites * cfg.tile_sites);
+  chunk = std::min<int64_t>(chunk, f.n_sites);
+  const size_t a_bytes = (size_t)(chunk * a_site), c_bytes = (size_t)(chunk * c_site);
+  const size_t need = (a_bytes + 255) / 256 * 256 + c_bytes;
+  if (need > h->hbuf_bytes) {
+    if (h->fault & kFaultAlloc) return fail(h, SU3_ERR_FAULT_INJECTED, "fault injected at alloc");
+    cudaDeviceSynchronize();
+    for (int i = 0; i < kHostBuffers; ++i) {
+      cudaFree(h->hbuf_dev[i]);
+      h->hbuf_dev[i] = nullptr;
+    }
+    h->hbuf_bytes = 0;
+    for (int i = 0; i < kHostBuffers; ++i) {
+      e = cudaMalloc((void**)&h->hbuf_dev[i], need);
+      if (e != cudaSuccess) return cuda_err(h, "cudaMalloc (host-path staging)", e);
+    }
+    h->hbuf_bytes = need;
+  }
+  cudaStream_t user = (cudaStream_t)stream;
+  e = cudaEventRecord(h->ev_start, user);
+  if (e != cudaSuccess) return cuda_err(h, "cudaEventRecord", e);
+  for (cudaStream_t st : {h->s_h2d, h->s_comp, h->s_d2h}) cudaStreamWaitEvent(st, h->ev_start, 0);
+  const size_t c_off = (a_bytes + 255) / 256 * 256;
+  const int64_t n_chunks = (f.n_sites + chunk - 1) / chunk;
+  for (int64_t i = 0; i < n_chunks; ++i) {
+    const int bi = (int)(i % kHostBuffers);
+    const int64_t first = i * chunk;
+    const int64_t ns = std::min<int64_t>(chunk, f.n_sites - first);
+    unsigned char* abuf = h->hbuf_dev[bi];
+    unsigned char* cbuf = h->hbuf_dev[bi] + c_off;
+    if (i >= kHostBuffers) cudaStreamWaitEvent(h->s_h2d, h->ev_d2h[bi], 0);  // buffer free again
+    e = cudaMemcpyAsync(abuf, (const unsigned char*)a_host + first * a_site, (size_t)(ns * a_site),
+                        cudaMemcpyHostToDevice, h->s_h2d);
+    if (e != cudaSuccess) return cuda_err(h, "cudaMemcpyAsync H2D", e);
+    cudaEventRecord(h->ev_h2d[bi], h->s_h2d);
+    cudaStreamWaitEvent(h->s_comp, h->ev_h2d[bi], 0);
+    Form fc = f;
+    fc.n_sites = ns;
+    s = launch_mult(fc, cfg, abuf, b, cbuf, ctx_of(h, h->s_comp));
+    if (s != SU3_OK) return s;
+    cudaEventRecord(h->ev_comp[bi], h->s_comp);
+    cudaStreamWaitEvent(h->s_d2h, h->ev_comp[bi], 0);
+    e = cudaMemcpyAsync((unsigned char*)c_host + first * c_site, cbuf, (size_t)(ns * c_site),
+                        cudaMemcpyDeviceToHost, h->s_d2h);
+    if (e != cudaSuccess) return cuda_err(h, "cudaMemcpyAsync D2H", e);
+    cudaEventRecord(h->ev_d2h[bi], h->s_d2h);
+  }
+  e = cudaStreamSynchronize(h->s_d2h);
+  if (e != cudaSuccess) return cuda_err(h, "host-path completion", e);
+  return su3_sync(h, h->s_comp, -1);
+}
+
+// ---- batched --------------------------------------------------------------------------------
+
+// Validates the items and writes the descriptors of the non-empty lattices; *m = their number.
+static su3_status fill_batch(su3_handle* h, int32_t n, const su3_batch_item* items, BatchDesc* out, int* total,
+                             int* m_out) {
+  int tiles = 0, m = 0;
+  for (int i = 0; i < n; ++i) {
+    const su3_batch_item& it = items[i];
+    const su3_desc& d = it.desc;
+    if (su3_check_desc(&d) != SU3_OK) return fail(h, SU3_ERR_INVALID_ARG, "invalid descriptor in batch item " + std::to_string(i));
+    if ((d.dtype != SU3_F64 && d.dtype != SU3_F32) || d.repr != SU3_REPR_FULL18 || d.layout != SU3_LAYOUT_AOS ||
+        d.arith != SU3_ARITH_NATIVE || (d.site_stride_bytes != 0 && d.site_stride_bytes != 4 * link_bytes(d.dtype, d.repr)))
+      return fail(h, SU3_ERR_UNSUPPORTED, "batched items must be F64 or F32, FULL18, packed AOS, NATIVE");
+    if (d.n_sites == 0) continue;
+    if (!it.a_dev || !it.c_dev || !aligned16(it.a_dev) || !aligned16(it.c_dev))
+      return fail(h, SU3_ERR_INVALID_ARG, "null or misaligned pointer in batch item " + std::to_string(i));
+    const int64_t nb = su3_array_bytes(&d);
+    if (it.a_dev != it.c_dev && ranges_overlap(it.a_dev, nb, it.c_dev, nb))
+      return fail(h, SU3_ERR_INVALID_ARG, "a and c overlap in batch item " + std::to_string(i));
+    BatchDesc& o = out[m++];
+    o.a = it.a_dev;
+    o.c = it.c_dev;
+    o.n_sites = d.n_sites;
+    o.dtype = d.dtype;
+    o.first_tile = tiles;
+    memcpy(o.b, it.b, sizeof(o.b));
+    const int64_t t = batch_tile_count(d.n_sites, h->bcfg.tile_sites);
+    if ((int64_t)tiles + t > (1ll << 30)) return fail(h, SU3_ERR_INVALID_ARG, "batch too large");
+    tiles += (int)t;
+  }
+  *total = tiles;
+  *m_out = m;
+  return SU3_OK;
+}
+
+static su3_status ensure_batch_buffers(su3_handle* h, int n, bool graph) {
+  BatchDesc** dv = graph ? &h->gdesc_dev : &h->bdesc_dev;
+  BatchDesc** hv = graph ? &h->gdesc_host : &h->bdesc_host;
+  int* cap = graph ? &h->gcap : &h->bcap;
+  if (n <= *cap) return SU3_OK;
+  if (h->fault & kFaultAlloc) return fail(h, SU3_ERR_FAULT_INJECTED, "fault injected at alloc");
+  cudaDeviceSynchronize();
+  cudaFree(*dv);
+  cudaFreeHost(*hv);
+  *dv = nullptr;
+  *hv = nullptr;
+  *cap = 0;
+  const int want = std::max(n, 128);
+  cudaError_t e = cudaMalloc((void**)dv, sizeof(BatchDesc) * want);
+  if (e == cudaSuccess) e = cudaMallocHost((void**)hv, sizeof(BatchDesc) * want);
+  if (e != cudaSuccess) return cuda_err(h, "allocating the batched workspace", e);
+  *cap = want;
+  return SU3_OK;
+}
+
+su3_status su3_mult_batched(su3_handle* h, int32_t n, const su3_batch_item* items, void* stream, int32_t use_graph) {
+  if (!h) return SU3_ERR_NOT_INITIALIZED;
+  if (n < 0 || (n > 0 && !items)) return fail(h, SU3_ERR_INVALID_ARG, "bad item count or null items");
+  if (n == 0) return SU3_OK;
+  if (h->fault & kFaultLaunch) return fail(h, SU3_ERR_FAULT_INJECTED, "fault injected at launch");
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaError_t e;
+  if (!use_graph) {
+    su3_status s = ensure_batch_buffers(h, n, false);
+    if (s != SU3_OK) return s;
+    if (h->bcopy_pending) {  // the previous upload must have left the pinned buffer
+      cudaEventSynchronize(h->bcopy_done);
+      h->bcopy_pending = false;
+    }
+    int total = 0, m = 0;
+    std::vector<BatchDesc> tmp(n);
+    s = fill_batch(h, n, items, tmp.data(), &total, &m);
+    if (s != SU3_OK) return s;
+    if (total == 0) return SU3_OK;
+    memcpy(h->bdesc_host, tmp.data(), sizeof(BatchDesc) * m);
+    if (h->fault & kFaultCopy) return fail(h, SU3_ERR_FAULT_INJECTED, "fault injected at copy");
+    e = cudaMemcpyAsync(h->bdesc_dev, h->bdesc_host, sizeof(BatchDesc) * m, cudaMemcpyHostToDevice, st);
+    if (e != cudaSuccess) return cuda_err(h, "uploading batch descriptors", e);
+    if (!h->bcopy_done) cudaEventCreateWithFlags(&h->bcopy_done, cudaEventDisableTiming);
+    cudaEventRecord(h->bcopy_done, st);
+    h->bcopy_pending = true;
+    return launch_batched(h->bdesc_dev, m, total, h->bcfg, ctx_of(h, st));
+  }
+  // graph mode: key = the raw item list; rebuild the graph when it changes
+  std::vector<char> key((const char*)items, (const char*)items + sizeof(su3_batch_item) * n);
+  if (!h->gexec || key != h->gkey) {
+    su3_status s = ensure_batch_buffers(h, n, true);
+    if (s != SU3_OK) return s;
+    int total = 0, m = 0;
+    std::vector<BatchDesc> tmp(n);
+    s = fill_batch(h, n, items, tmp.data(), &total, &m);
+    if (s != SU3_OK) return s;
+    if (total == 0) return SU3_OK;
+    s = prepare_batched(h->bcfg, &h->err);  // kernel attributes are set outside the capture
+    if (s != SU3_OK) return s;
+    cudaDeviceSynchronize();  // earlier replays may still read the descriptor buffers
+    if (h->gexec) {
+      cudaGraphExecDestroy(h->gexec);
+      h->gexec = nullptr;
+    }
+    memcpy(h->gdesc_host, tmp.data(), sizeof(BatchDesc) * m);
+    if (!h->cap_stream) {
+      e = cudaStreamCreateWithFlags(&h->cap_stream, cudaStreamNonBlocking);
+      if (e != cudaSuccess) return cuda_err(h, "cudaStreamCreate", e);
+    }
+    cudaGraph_t g;
+    e = cudaStreamBeginCapture(h->cap_stream, cudaStreamCaptureModeThreadLocal);
+    if (e != cudaSuccess) return cuda_err(h, "cudaStreamBeginCapture", e);
+    cudaMemcpyAsync(h->gdesc_dev, h->gdesc_host, sizeof(BatchDesc) * m, cudaMemcpyHostToDevice, h->cap_stream);
+    const int64_t before = h->launches;
+    s = launch_batched(h->gdesc_dev, m, total, h->bcfg, ctx_of(h, h->cap_stream));
+    h->launches = before;  // counted at replay
+    e = cudaStreamEndCapture(h->cap_stream, &g);
+    if (s != SU3_OK) return s;
+    if (e != cudaSuccess) return cuda_err(h, "cudaStreamEndCapture", e);
+    e = cudaGraphInstantiate(&h->gexec, g, 0);
+    cudaGraphDestroy(g);
+    if (e != cudaSuccess) return cuda_err(h, "cudaGraphInstantiate", e);
+    h->gkey.swap(key);
+  }
+  e = cudaGraphLaunch(h->gexec, st);
+  if (e != cudaSuccess) return cuda_err(h, "cudaGraphLaunch", e);
+  ++h->launches;
+  return SU3_OK;
+}
+
+}  // extern "C"

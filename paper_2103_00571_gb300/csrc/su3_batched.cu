@@ -1,0 +1,202 @@
+// Batched SU3_Bench link multiply: many independent lattices (uneven extents, FP64 or FP32
+// storage, each with its own four b matrices) in ONE persistent launch.
+//
+// The tiles of all lattices form one global work list (lattice l owns tiles
+// first_tile[l] .. first_tile[l+1]-1). Each CTA strides over that list with the same shared-memory
+// bulk-copy ring as the single-lattice AOS kernel; the thread issuing a tile's copy looks its
+// lattice up by binary search over first_tile and leaves (lattice, first site, sites, dtype) next
+// to the stage, where the computing threads read it after the stage's mbarrier completes. Each
+// tile's link products use that lattice's b (read through the L1 cache; FP32 lattices round it to
+// FP32 once per load).
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "su3_device.cuh"
+#include "su3_internal.h"
+
+namespace su3 {
+
+struct TileInfo {
+  int lattice;
+  int nt;  // sites in this tile
+  long long first_site;
+};
+
+struct BatchArgs {
+  const BatchDesc* descs;
+  int n;
+  int total_tiles;
+  int tile_sites;
+  int stages;
+  unsigned stage_bytes;
+  unsigned* status;
+};
+
+constexpr int kBatchHeader = 1024;  // mbarriers (<= 8) + TileInfo per stage (<= 8 x 16 B)
+
+template <int DT>
+__device__ __forceinline__ void batch_tile_compute(unsigned char* in, int nt, const BatchDesc& d) {
+  using S = Storage<DT>;
+  using A = typename S::acc;
+  using V = typename S::vec;
+  constexpr int kLink = 9 * (int)sizeof(V);
+  const int j = threadIdx.x & 3;
+  A bre[9], bim[9];
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    bre[e] = (A)__ldg(&d.b[18 * j + 2 * e]);
+    bim[e] = (A)__ldg(&d.b[18 * j + 2 * e + 1]);
+  }
+  for (int q = threadIdx.x; q < 4 * nt; q += blockDim.x) {
+    V* p = reinterpret_cast<V*>(in + (size_t)q * kLink);
+    Link<A> la, lc;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) S::unpack(p[e], la.re[e], la.im[e]);
+    link_mult<3>(la, bre, bim, lc);
+#pragma unroll
+    for (int e = 0; e < 9; ++e) p[e] = S::pack(lc.re[e], lc.im[e]);
+  }
+}
+
+__global__ void __launch_bounds__(256) su3_batched_kernel(const __grid_constant__ BatchArgs p) {
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+  TileInfo* info = reinterpret_cast<TileInfo*>(smem + 128);
+  unsigned char* stage0 = smem + kBatchHeader;
+  const int tid = threadIdx.x;
+  const int S_ = p.stages;
+  if (tid == 0) {
+    for (int s = 0; s < S_; ++s) mbar_init(&full[s], 1);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  const uint64_t pol = policy_evict_first();
+  const int my_tiles =
+      p.total_tiles > (int)blockIdx.x ? (p.total_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+
+  // thread 0 only: find the tile's lattice, record it beside the stage, start the copy
+  auto issue_load = [&](int k) {
+    const int t = (int)blockIdx.x + k * (int)gridDim.x;
+    int lo = 0, hi = p.n - 1;  // last lattice with first_tile <= t
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (p.descs[mid].first_tile <= t) lo = mid; else hi = mid - 1;
+    }
+    const BatchDesc& d = p.descs[lo];
+    const long long first = (long long)(t - d.first_tile) * p.tile_sites;
+    long long rest = d.n_sites - first;
+    const int nt = (int)(rest < p.tile_sites ? rest : p.tile_sites);
+    const int s = k % S_;
+    info[s].lattice = lo;
+    info[s].nt = nt > 0 ? nt : 0;
+    info[s].first_site = first;
+    const long long site_bytes = d.dtype == SU3_F64 ? 576 : 288;
+    const unsigned bytes = (unsigned)(info[s].nt * site_bytes);
+    mbar_arrive_expect_tx(&full[s], bytes);
+    if (bytes) bulk_g2s(stage0 + (size_t)s * p.stage_bytes, static_cast<const unsigned char*>(d.a) + first * site_bytes,
+                        bytes, &full[s], pol);
+  };
+
+  const int prefetch = S_ - 1;
+  int issued = my_tiles < prefetch ? my_tiles : prefetch;
+  if (tid == 0)
+    for (int k = 0; k < issued; ++k) issue_load(k);
+
+  int kfail = -1;
+  for (int k = 0; k < my_tiles; ++k) {
+    const int s = k % S_;
+    const bool ok = mbar_wait_bounded(&full[s], (unsigned)((k / S_) & 1));
+    unsigned char* in = stage0 + (size_t)s * p.stage_bytes;
+    const TileInfo ti = info[s];
+    const BatchDesc& d = p.descs[ti.lattice];
+    const int dtype = d.dtype;
+    if (ok) {
+      if (dtype == SU3_F64) batch_tile_compute<kF64>(in, ti.nt, d);
+      else batch_tile_compute<kF32>(in, ti.nt, d);
+    }
+    fence_proxy_async_smem();
+    if (__syncthreads_or(!ok)) {
+      kfail = k;
+      break;
+    }
+    if (tid < 32) {
+      if (tid == 0 && ti.nt > 0) {
+        const long long site_bytes = dtype == SU3_F64 ? 576 : 288;
+        bulk_s2g(static_cast<unsigned char*>(d.c) + ti.first_site * site_bytes, in, (unsigned)(ti.nt * site_bytes), pol);
+      }
+      bulk_commit();
+      bulk_wait_read<1>();
+      __syncwarp();
+      if (tid == 0 && issued < my_tiles) issue_load(issued++);
+    }
+  }
+  if (kfail >= 0 && tid == 0) {
+    atomicOr(p.status, kDevErrTimeout);
+    // let the loads still in flight land before shared memory is released (bounded)
+    for (int k = kfail; k < issued; ++k) mbar_wait_bounded(&full[k % S_], (unsigned)((k / S_) & 1));
+  }
+  if (tid < 32) bulk_wait_all<0>();
+}
+
+BatchCfg default_batch_cfg() {
+  BatchCfg c;
+  c.block = 128;
+  c.tile_sites = 32;
+  c.stages = 4;
+  c.ctas_per_sm = 2;
+  return c;
+}
+
+int batch_tile_count(long long n_sites, int tile_sites) { return (int)((n_sites + tile_sites - 1) / tile_sites); }
+
+static size_t batch_smem(const BatchCfg& cfg) {
+  return kBatchHeader + (size_t)cfg.stages * (((size_t)cfg.tile_sites * 576 + 127) / 128 * 128);
+}
+
+su3_status prepare_batched(const BatchCfg& cfg, std::string* err) {
+  const size_t smem = batch_smem(cfg);
+  if (smem > 227 * 1024 || cfg.stages < 2 || cfg.stages > 8 || cfg.tile_sites < 1 || cfg.block < 32 ||
+      cfg.block > 256 || cfg.block % 32) {
+    *err = "batched launch configuration exceeds shared memory, stage or block limits";
+    return SU3_ERR_INVALID_ARG;
+  }
+  cudaError_t e = cudaFuncSetAttribute(su3_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) {
+    *err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
+    return SU3_ERR_CUDA;
+  }
+  return SU3_OK;
+}
+
+su3_status launch_batched(const BatchDesc* descs_dev, int n, int total_tiles, const BatchCfg& cfg,
+                          const LaunchCtx& ctx) {
+  if (total_tiles == 0) return SU3_OK;
+  BatchArgs p;
+  p.descs = descs_dev;
+  p.n = n;
+  p.total_tiles = total_tiles;
+  p.tile_sites = cfg.tile_sites;
+  p.stages = cfg.stages;
+  p.stage_bytes = (unsigned)(((long long)cfg.tile_sites * 576 + 127) / 128 * 128);
+  p.status = ctx.status;
+  const size_t smem = batch_smem(cfg);
+  cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+  cudaStreamIsCapturing(ctx.stream, &cs);
+  if (cs == cudaStreamCaptureStatusNone) {
+    su3_status s = prepare_batched(cfg, ctx.err);
+    if (s != SU3_OK) return s;
+  }
+  cudaError_t e;
+  const int grid = std::min(total_tiles, ctx.num_sms * cfg.ctas_per_sm);
+  su3_batched_kernel<<<grid, cfg.block, smem, ctx.stream>>>(p);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    *ctx.err = std::string("su3_batched_kernel launch: ") + cudaGetErrorString(e);
+    return SU3_ERR_CUDA;
+  }
+  ++*ctx.launches;
+  return SU3_OK;
+}
+
+}  // namespace su3

@@ -1,0 +1,248 @@
+// Device-side building blocks of libsu3 (sm_103a): PTX wrappers for mbarriers, bulk async copies
+// and cache-hinted vector memory operations, storage conversions, and the 3x3 complex link
+// product of the SU3_Bench kernel (arXiv 2103.00571, §Background "SU3_Bench").
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace su3 {
+
+// Upper bound on any spin-wait, in globaltimer nanoseconds.
+constexpr unsigned long long kWaitLimitNs = 4000000000ull;
+
+enum Dtype { kF64 = 0, kF32 = 1, kF16 = 2, kBF16 = 3 };
+
+// ---- PTX wrappers -----------------------------------------------------------------------------
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ unsigned long long globaltimer_ns() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ __forceinline__ void mbar_init(uint64_t* bar, unsigned count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count) : "memory");
+}
+
+__device__ __forceinline__ void fence_mbar_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(uint64_t* bar, unsigned bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, unsigned parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+
+// Waits for phase `parity` of an mbarrier; gives up after `limit_ns` and returns false.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, unsigned parity,
+                                                  unsigned long long limit_ns = kWaitLimitNs) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer_ns();
+  for (;;) {
+    if (mbar_try_wait(bar, parity)) return true;
+    if (globaltimer_ns() - t0 > limit_ns) return false;
+  }
+}
+
+// 1-D bulk async copy global -> this CTA's shared memory, completing `bytes` on `bar`.
+// Both addresses 16-byte aligned, bytes a multiple of 16 (checked by the callers' invariants).
+__device__ __forceinline__ void bulk_g2s(void* sdst, const void* gsrc, unsigned bytes, uint64_t* bar,
+                                         uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint [%0], [%1], "
+      "%2, [%3], %4;" ::"r"(smem_u32(sdst)),
+      "l"(gsrc), "r"(bytes), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
+}
+
+// 1-D bulk async copy shared -> global, tracked by this thread's bulk groups.
+__device__ __forceinline__ void bulk_s2g(void* gdst, const void* ssrc, unsigned bytes, uint64_t policy) {
+  asm volatile("cp.async.bulk.global.shared::cta.bulk_group.L2::cache_hint [%0], [%1], %2, %3;" ::"l"(gdst),
+               "r"(smem_u32(ssrc)), "r"(bytes), "l"(policy)
+               : "memory");
+}
+
+__device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
+
+template <int N>
+__device__ __forceinline__ void bulk_wait_read() {
+  asm volatile("cp.async.bulk.wait_group.read %0;" ::"n"(N) : "memory");
+}
+
+template <int N>
+__device__ __forceinline__ void bulk_wait_all() {
+  asm volatile("cp.async.bulk.wait_group %0;" ::"n"(N) : "memory");
+}
+
+// Orders this thread's generic-proxy shared-memory writes before later async-proxy reads.
+__device__ __forceinline__ void fence_proxy_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+
+__device__ __forceinline__ uint64_t policy_evict_first() {
+  uint64_t p;
+  asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(p));
+  return p;
+}
+
+// ---- streaming global loads/stores (read once: no L1 allocation; write once: evict-first) ----
+
+__device__ __forceinline__ double2 ldg_stream(const double2* p) {
+  double2 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v2.f64 {%0, %1}, [%2];" : "=d"(v.x), "=d"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ float2 ldg_stream(const float2* p) {
+  float2 v;
+  asm volatile("ld.global.nc.L1::no_allocate.v2.f32 {%0, %1}, [%2];" : "=f"(v.x), "=f"(v.y) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ uint32_t ldg_stream(const uint32_t* p) {
+  uint32_t v;
+  asm volatile("ld.global.nc.L1::no_allocate.b32 %0, [%1];" : "=r"(v) : "l"(p));
+  return v;
+}
+__device__ __forceinline__ void stg_stream(double2* p, double2 v) {
+  asm volatile("st.global.cs.v2.f64 [%0], {%1, %2};" ::"l"(p), "d"(v.x), "d"(v.y) : "memory");
+}
+__device__ __forceinline__ void stg_stream(float2* p, float2 v) {
+  asm volatile("st.global.cs.v2.f32 [%0], {%1, %2};" ::"l"(p), "f"(v.x), "f"(v.y) : "memory");
+}
+__device__ __forceinline__ void stg_stream(uint32_t* p, uint32_t v) {
+  asm volatile("st.global.cs.b32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+
+// ---- storage <-> arithmetic conversions --------------------------------------------------------
+// A "complex element" of storage type T is stored as one vector: double2 (F64), float2 (F32),
+// or a 32-bit word holding two 16-bit reals (F16/BF16), re in the low half.
+
+template <int DT>
+struct Storage;
+
+template <>
+struct Storage<kF64> {
+  using real = double;   // storage real
+  using vec = double2;   // one complex element in memory
+  using acc = double;    // arithmetic type
+  static constexpr int real_bytes = 8;
+  __device__ static __forceinline__ void unpack(vec v, acc& re, acc& im) { re = v.x; im = v.y; }
+  __device__ static __forceinline__ vec pack(acc re, acc im) { return make_double2(re, im); }
+};
+
+template <>
+struct Storage<kF32> {
+  using real = float;
+  using vec = float2;
+  using acc = float;
+  static constexpr int real_bytes = 4;
+  __device__ static __forceinline__ void unpack(vec v, acc& re, acc& im) { re = v.x; im = v.y; }
+  __device__ static __forceinline__ vec pack(acc re, acc im) { return make_float2(re, im); }
+};
+
+template <>
+struct Storage<kF16> {
+  using real = __half;
+  using vec = uint32_t;
+  using acc = float;
+  static constexpr int real_bytes = 2;
+  __device__ static __forceinline__ void unpack(vec v, acc& re, acc& im) {
+    __half2 h = *reinterpret_cast<__half2*>(&v);
+    float2 f = __half22float2(h);
+    re = f.x;
+    im = f.y;
+  }
+  __device__ static __forceinline__ vec pack(acc re, acc im) {
+    __half2 h = __floats2half2_rn(re, im);  // both halves rounded to nearest even
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+};
+
+template <>
+struct Storage<kBF16> {
+  using real = __nv_bfloat16;
+  using vec = uint32_t;
+  using acc = float;
+  static constexpr int real_bytes = 2;
+  __device__ static __forceinline__ void unpack(vec v, acc& re, acc& im) {
+    re = __uint_as_float(v << 16);          // a bfloat16 is the top half of a binary32
+    im = __uint_as_float(v & 0xffff0000u);
+  }
+  __device__ static __forceinline__ vec pack(acc re, acc im) {
+    __nv_bfloat162 h = __floats2bfloat162_rn(re, im);
+    return *reinterpret_cast<uint32_t*>(&h);
+  }
+};
+
+// ---- the link product -------------------------------------------------------------------------
+
+// A link in registers: up to 9 complex elements, row major (e = 3*row + col).
+template <typename T>
+struct Link {
+  T re[9], im[9];
+};
+
+// Row 2 of an SU(3) matrix from rows 0 and 1: conj(row0 x row1), with
+// (u x v)_k = u_p v_q - u_q v_p, (p, q) = (k+1, k+2) mod 3.
+template <typename T>
+__device__ __forceinline__ void rebuild_row2(Link<T>& a) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int p = (k + 1) % 3, q = (k + 2) % 3;
+    T xr = a.re[p] * a.re[3 + q];
+    xr = fma(-a.im[p], a.im[3 + q], xr);
+    xr = fma(-a.re[q], a.re[3 + p], xr);
+    xr = fma(a.im[q], a.im[3 + p], xr);
+    T xi = a.re[p] * a.im[3 + q];
+    xi = fma(a.im[p], a.re[3 + q], xi);
+    xi = fma(-a.re[q], a.im[3 + p], xi);
+    xi = fma(-a.im[q], a.re[3 + p], xi);
+    a.re[6 + k] = xr;
+    a.im[6 + k] = -xi;
+  }
+}
+
+// c[k][l] = sum_m a[k][m] b[m][l] for rows k < ROWS (the SU3_Bench kernel's inner k, l, m loops;
+// 4 real FMAs per complex multiply-accumulate).
+template <int ROWS, typename T>
+__device__ __forceinline__ void link_mult(const Link<T>& a, const T (&bre)[9], const T (&bim)[9],
+                                          Link<T>& c) {
+#pragma unroll
+  for (int k = 0; k < ROWS; ++k) {
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      T re = a.re[3 * k] * bre[l];
+      T im = a.re[3 * k] * bim[l];
+      re = fma(-a.im[3 * k], bim[l], re);
+      im = fma(a.im[3 * k], bre[l], im);
+#pragma unroll
+      for (int m = 1; m < 3; ++m) {
+        re = fma(a.re[3 * k + m], bre[3 * m + l], re);
+        re = fma(-a.im[3 * k + m], bim[3 * m + l], re);
+        im = fma(a.re[3 * k + m], bim[3 * m + l], im);
+        im = fma(a.im[3 * k + m], bre[3 * m + l], im);
+      }
+      c.re[3 * k + l] = re;
+      c.im[3 * k + l] = im;
+    }
+  }
+}
+
+}  // namespace su3

@@ -1,0 +1,88 @@
+// Host-side internals shared by the libsu3 translation units (not part of the C ABI).
+#pragma once
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+
+#include "su3.h"
+
+namespace su3 {
+
+// Device status word bits (the handle's status word; su3_sync reads and clears it).
+enum : unsigned { kDevErrTimeout = 1u };
+
+// A fully validated form: what a kernel instantiation is selected by.
+struct Form {
+  int dtype;      // su3_dtype
+  int repr_in;    // su3_repr of a
+  int repr_out;   // su3_repr of c
+  int layout;     // su3_layout
+  int arith;      // su3_arith
+  int64_t n_sites;
+  int64_t a_stride;  // AOS: bytes between sites of a (resolved, never 0)
+  int64_t c_stride;  // AOS: bytes between sites of c
+};
+
+struct LaunchCfg {
+  int block;
+  int tile_sites;
+  int stages;
+  int ctas_per_sm;
+};
+
+// Everything a launcher needs from the handle.
+struct LaunchCtx {
+  cudaStream_t stream;
+  unsigned* status;  // device status word
+  int num_sms;
+  int64_t* launches;  // incremented per kernel launch
+  std::string* err;
+};
+
+inline int real_bytes(int dtype) { return dtype == SU3_F64 ? 8 : dtype == SU3_F32 ? 4 : 2; }
+inline int n_elem(int repr) { return repr == SU3_REPR_FULL18 ? 9 : 6; }
+inline int64_t link_bytes(int dtype, int repr) { return (int64_t)n_elem(repr) * 2 * real_bytes(dtype); }
+
+// Default launch configuration of a form (used until the autotuner sets one).
+LaunchCfg default_cfg(const Form& f);
+
+// c = a x b over one lattice (the streaming kernels). b is FP64 on the host.
+su3_status launch_mult(const Form& f, const LaunchCfg& cfg, const void* a, const double* b, void* c,
+                       const LaunchCtx& ctx);
+
+// One CTA whose bounded mbarrier wait runs out after limit_ms (failure-path self test).
+su3_status launch_selftest_wait(int limit_ms, const LaunchCtx& ctx);
+
+// Packed FP64 AOS <-> the form's storage.
+su3_status launch_pack(const Form& dst, const double* src, void* dst_dev, const LaunchCtx& ctx);
+su3_status launch_unpack(const Form& src, const void* src_dev, double* dst, const LaunchCtx& ctx);
+
+// Device descriptor of one lattice in a batched launch.
+struct BatchDesc {
+  const void* a;
+  void* c;
+  long long n_sites;
+  int dtype;           // SU3_F64 or SU3_F32
+  int first_tile;      // exclusive prefix sum of tile counts
+  double b[72];        // FP64 b (F32 lattices round it in the kernel)
+};
+
+struct BatchCfg {
+  int block;
+  int tile_sites;
+  int stages;
+  int ctas_per_sm;
+};
+
+BatchCfg default_batch_cfg();
+int batch_tile_count(long long n_sites, int tile_sites);
+
+// Validates a batched configuration and sets the kernel's shared-memory attribute.
+su3_status prepare_batched(const BatchCfg& cfg, std::string* err);
+
+// One persistent launch over `n` lattices whose descriptors are already in device memory.
+su3_status launch_batched(const BatchDesc* descs_dev, int n, int total_tiles, const BatchCfg& cfg,
+                          const LaunchCtx& ctx);
+
+}  // namespace su3

@@ -1,0 +1,381 @@
+// Streaming kernels of the SU3_Bench link multiply (arXiv 2103.00571, §Background "SU3_Bench"):
+// c[i].link[j] = a[i].link[j] x b[j] for every site i and link j.
+//
+// The paper's own analysis (§Background) puts the time in streaming A in and C out with no reuse
+// and B cache-resident. On GB300 that means: move a and c between HBM and shared memory with
+// 1-D bulk async copies (the TMA engine), keep b in registers (each thread always serves the same
+// link direction j), and spend the SM only on the 108 FMAs of each link.
+//
+//  * AOS (the benchmark's Site array): a persistent CTA streams tiles of whole sites through a
+//    `stages`-deep ring of shared-memory buffers. Each tile arrives by one bulk copy completing on
+//    an mbarrier; each thread multiplies links q = tid, tid+block, ... of the tile (link stride in
+//    shared memory 144/96/72/48/36/24 B, all bank-conflict-free or 2-way) and writes the result
+//    back in place; warp 0 then bulk-stores the tile and refills the ring. Site bytes past the four
+//    links (the paper's coordinates, index, parity and pad) are never written: with such a stride
+//    the store is one bulk copy per site.
+//  * SOA / AOSOA32: the element-major layouts are coalesced as they stand, so a thread loads its
+//    links directly with 8/16-byte no-L1-allocate loads and writes with streaming stores.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+
+#include "su3_device.cuh"
+#include "su3_internal.h"
+
+namespace su3 {
+
+template <typename A>
+struct BMat {
+  A v[72];  // b[j][row][col][re/im]
+};
+
+template <typename A>
+struct AosArgs {
+  const unsigned char* a;
+  unsigned char* c;
+  long long n_sites;
+  long long a_stride;  // bytes
+  long long c_stride;  // bytes
+  int tile_sites;
+  int stages;
+  int n_tiles;
+  unsigned stage_bytes;  // bytes reserved per input stage (multiple of 128)
+  unsigned out_bytes;    // bytes per output buffer (separate-output forms)
+  unsigned* status;
+  BMat<A> b;
+};
+
+constexpr int kSmemHeader = 1024;  // mbarriers (<= 8 x 8 B) + b (<= 576 B), then 128-aligned data
+
+// Loads this thread's b[j] (j = tid % 4) into registers via shared memory.
+template <typename A>
+__device__ __forceinline__ void load_b_regs(const BMat<A>& b, A* bsh, A (&bre)[9], A (&bim)[9]) {
+  for (int i = threadIdx.x; i < 72; i += blockDim.x) bsh[i] = b.v[i];
+  __syncthreads();
+  const int j = threadIdx.x & 3;
+#pragma unroll
+  for (int e = 0; e < 9; ++e) {
+    bre[e] = bsh[18 * j + 2 * e];
+    bim[e] = bsh[18 * j + 2 * e + 1];
+  }
+}
+
+// NE_IN complex elements per input link (9 full, 6 two-row); ROWS_OUT rows of c (3 or 2).
+// In place (ROWS_OUT*3 == NE_IN): the result overwrites the input tile in shared memory.
+// Otherwise (two-row in, full out) results go to a ring of 3 output buffers.
+template <int DT, int NE_IN, int ROWS_OUT>
+__global__ void __launch_bounds__(256) su3_aos_kernel(const __grid_constant__ AosArgs<typename Storage<DT>::acc> p) {
+  using S = Storage<DT>;
+  using A = typename S::acc;
+  using V = typename S::vec;
+  constexpr int NE_OUT = 3 * ROWS_OUT;
+  constexpr bool kInPlace = (NE_OUT == NE_IN);
+  constexpr int kLinkIn = NE_IN * (int)sizeof(V);
+  constexpr int kLinkOut = NE_OUT * (int)sizeof(V);
+
+  extern __shared__ __align__(128) unsigned char smem[];
+  uint64_t* full = reinterpret_cast<uint64_t*>(smem);
+  A* bsh = reinterpret_cast<A*>(smem + 64);
+  unsigned char* stage0 = smem + kSmemHeader;
+  unsigned char* out0 = stage0 + (size_t)p.stages * p.stage_bytes;
+
+  const int tid = threadIdx.x;
+  const int S_ = p.stages;
+  if (tid == 0) {
+    for (int s = 0; s < S_; ++s) mbar_init(&full[s], 1);
+    fence_mbar_init();
+  }
+  A bre[9], bim[9];
+  load_b_regs(p.b, bsh, bre, bim);  // contains __syncthreads (also publishes the mbarrier init)
+
+  const uint64_t pol = policy_evict_first();
+  const int my_tiles = p.n_tiles > (int)blockIdx.x ? (p.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
+  auto tile_of = [&](int k) { return (int)blockIdx.x + k * (int)gridDim.x; };
+  auto tile_nsites = [&](int t) {
+    long long first = (long long)t * p.tile_sites;
+    long long rest = p.n_sites - first;
+    return (int)(rest < p.tile_sites ? rest : p.tile_sites);
+  };
+  auto issue_load = [&](int k) {
+    const int t = tile_of(k);
+    const int s = k % S_;
+    const unsigned bytes = (unsigned)((long long)tile_nsites(t) * p.a_stride);
+    mbar_arrive_expect_tx(&full[s], bytes);
+    bulk_g2s(stage0 + (size_t)s * p.stage_bytes, p.a + (long long)t * p.tile_sites * p.a_stride, bytes,
+             &full[s], pol);
+  };
+
+  const int prefetch = kInPlace ? S_ - 1 : S_;
+  if (tid == 0)
+    for (int k = 0; k < prefetch && k < my_tiles; ++k) issue_load(k);
+
+  const bool packed_store = kInPlace ? (p.a_stride == 4 * kLinkIn && p.c_stride == 4 * kLinkOut)
+                                     : (p.c_stride == 4 * kLinkOut);
+  int issued = my_tiles < prefetch ? my_tiles : prefetch;  // loads issued so far (thread 0's view)
+  int kfail = -1;
+
+  for (int k = 0; k < my_tiles; ++k) {
+    const int s = k % S_;
+    const int t = tile_of(k);
+    const int nt = tile_nsites(t);
+    const bool ok = mbar_wait_bounded(&full[s], (unsigned)((k / S_) & 1));
+    unsigned char* in = stage0 + (size_t)s * p.stage_bytes;
+    unsigned char* out = kInPlace ? in : out0 + (size_t)(k % 3) * p.out_bytes;
+    if (ok) {
+      for (int q = tid; q < 4 * nt; q += blockDim.x) {
+        const int site = q >> 2, j = q & 3;
+        const V* src = reinterpret_cast<const V*>(in + (size_t)site * p.a_stride + j * kLinkIn);
+        Link<A> la, lc;
+#pragma unroll
+        for (int e = 0; e < NE_IN; ++e) S::unpack(src[e], la.re[e], la.im[e]);
+        if (NE_IN == 6 && ROWS_OUT == 3) rebuild_row2(la);
+        link_mult<ROWS_OUT>(la, bre, bim, lc);
+        V* dst = kInPlace ? const_cast<V*>(src) : reinterpret_cast<V*>(out + (size_t)q * kLinkOut);
+#pragma unroll
+        for (int e = 0; e < NE_OUT; ++e) dst[e] = S::pack(lc.re[e], lc.im[e]);
+      }
+    }
+    fence_proxy_async_smem();
+    if (!kInPlace && tid < 32) bulk_wait_read<1>();  // store(k-2) done reading out[(k+1)%3]
+    if (__syncthreads_or(!ok)) {
+      kfail = k;
+      break;
+    }
+    if (tid < 32) {
+      // store tile k
+      const long long first = (long long)t * p.tile_sites;
+      if (packed_store) {
+        if (tid == 0)
+          bulk_s2g(p.c + first * p.c_stride, out, (unsigned)(nt * 4 * kLinkOut), pol);
+      } else {
+        const long long src_stride = kInPlace ? p.a_stride : 4 * kLinkOut;
+        for (int i = tid; i < nt; i += 32)
+          bulk_s2g(p.c + (first + i) * p.c_stride, out + (size_t)i * src_stride, (unsigned)(4 * kLinkOut), pol);
+      }
+      bulk_commit();
+      if (kInPlace) {
+        bulk_wait_read<1>();  // store(k-1) has read stage (k-1) % S
+        __syncwarp();
+        if (tid == 0 && issued < my_tiles) issue_load(issued++);
+      } else if (tid == 0 && issued < my_tiles) {
+        issue_load(issued++);  // stage s was fully read before the barrier
+      }
+    }
+  }
+
+  if (kfail >= 0 && tid == 0) {
+    atomicOr(p.status, kDevErrTimeout);
+    // let the loads still in flight land before shared memory is released (bounded)
+    for (int k = kfail; k < issued; ++k) mbar_wait_bounded(&full[k % S_], (unsigned)((k / S_) & 1));
+  }
+  if (tid < 32) bulk_wait_all<0>();
+}
+
+// ---- SOA / AOSOA32: direct coalesced loads ----------------------------------------------------
+
+template <typename A>
+struct DirectArgs {
+  const void* a;
+  void* c;
+  long long n_links;
+  BMat<A> b;
+};
+
+template <int LAYOUT, int NE>
+__device__ __forceinline__ long long elem_index(long long q, int e, long long n_links) {
+  if (LAYOUT == SU3_LAYOUT_SOA) return (long long)e * n_links + q;
+  return ((q >> 5) * NE + e) * 32 + (q & 31);  // AOSOA32
+}
+
+template <int DT, int NE_IN, int ROWS_OUT, int LAYOUT, int LPT>
+__global__ void __launch_bounds__(256) su3_direct_kernel(const __grid_constant__ DirectArgs<typename Storage<DT>::acc> p) {
+  using S = Storage<DT>;
+  using A = typename S::acc;
+  using V = typename S::vec;
+  constexpr int NE_OUT = 3 * ROWS_OUT;
+  __shared__ A bsh[72];
+  A bre[9], bim[9];
+  load_b_regs(p.b, bsh, bre, bim);
+  const V* a = reinterpret_cast<const V*>(p.a);
+  V* c = reinterpret_cast<V*>(p.c);
+  const long long T = (long long)gridDim.x * blockDim.x;  // a multiple of 4: j stays tid % 4
+  for (long long base = (long long)blockIdx.x * blockDim.x + threadIdx.x; base < p.n_links; base += LPT * T) {
+    V buf[LPT][NE_IN];
+#pragma unroll
+    for (int u = 0; u < LPT; ++u) {
+      const long long q = base + u * T;
+      if (q < p.n_links) {
+#pragma unroll
+        for (int e = 0; e < NE_IN; ++e) buf[u][e] = ldg_stream(a + elem_index<LAYOUT, NE_IN>(q, e, p.n_links));
+      }
+    }
+#pragma unroll
+    for (int u = 0; u < LPT; ++u) {
+      const long long q = base + u * T;
+      if (q < p.n_links) {
+        Link<A> la, lc;
+#pragma unroll
+        for (int e = 0; e < NE_IN; ++e) S::unpack(buf[u][e], la.re[e], la.im[e]);
+        if (NE_IN == 6 && ROWS_OUT == 3) rebuild_row2(la);
+        link_mult<ROWS_OUT>(la, bre, bim, lc);
+#pragma unroll
+        for (int e = 0; e < NE_OUT; ++e) stg_stream(c + elem_index<LAYOUT, NE_OUT>(q, e, p.n_links), S::pack(lc.re[e], lc.im[e]));
+      }
+    }
+  }
+}
+
+// ---- failure-path self test ------------------------------------------------------------------
+
+// One CTA waits on an mbarrier that expects two arrivals but gets one, with a short limit; the
+// bounded wait gives up, the kernel records the timeout and returns.
+__global__ void su3_selftest_wait_kernel(unsigned* status, unsigned long long limit_ns) {
+  __shared__ uint64_t bar;
+  if (threadIdx.x == 0) {
+    mbar_init(&bar, 2);
+    fence_mbar_init();
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_u32(&bar)) : "memory");
+  const bool ok = mbar_wait_bounded(&bar, 0u, limit_ns);
+  if (__syncthreads_or(!ok) && threadIdx.x == 0) atomicOr(status, kDevErrTimeout);
+}
+
+su3_status launch_selftest_wait(int limit_ms, const LaunchCtx& ctx) {
+  su3_selftest_wait_kernel<<<1, 32, 0, ctx.stream>>>(ctx.status, (unsigned long long)limit_ms * 1000000ull);
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) {
+    *ctx.err = std::string("su3_selftest_wait_kernel launch: ") + cudaGetErrorString(e);
+    return SU3_ERR_CUDA;
+  }
+  ++*ctx.launches;
+  return SU3_OK;
+}
+
+// ---- host launchers -----------------------------------------------------------------------------
+
+LaunchCfg default_cfg(const Form& f) {
+  LaunchCfg c;
+  if (f.layout == SU3_LAYOUT_AOS) {
+    c.block = 128;
+    // ~18 KB per tile for FP64 full sites, ~9-18 KB for the narrower forms
+    const int64_t site_in = f.a_stride;
+    int ts = (int)std::max<int64_t>(32, std::min<int64_t>(128, 18432 / std::max<int64_t>(site_in, 1)));
+    c.tile_sites = ts;
+    c.stages = 4;
+    c.ctas_per_sm = 2;
+  } else {
+    c.block = 256;
+    c.tile_sites = f.dtype == SU3_F64 ? 1 : f.dtype == SU3_F32 ? 2 : 4;  // links per thread
+    c.stages = 0;
+    c.ctas_per_sm = 4;
+  }
+  return c;
+}
+
+template <typename A>
+static BMat<A> make_b(const double* b) {
+  BMat<A> m;
+  for (int i = 0; i < 72; ++i) m.v[i] = (A)b[i];
+  return m;
+}
+
+static su3_status cuda_fail(const LaunchCtx& ctx, const char* what, cudaError_t e) {
+  *ctx.err = std::string(what) + ": " + cudaGetErrorString(e);
+  return SU3_ERR_CUDA;
+}
+
+template <int DT, int NE_IN, int ROWS_OUT>
+static su3_status run_aos(const Form& f, const LaunchCfg& cfg, const void* a, const double* b, void* c,
+                          const LaunchCtx& ctx) {
+  using A = typename Storage<DT>::acc;
+  using V = typename Storage<DT>::vec;
+  constexpr int NE_OUT = 3 * ROWS_OUT;
+  constexpr bool kInPlace = (NE_OUT == NE_IN);
+  AosArgs<A> p;
+  p.a = static_cast<const unsigned char*>(a);
+  p.c = static_cast<unsigned char*>(c);
+  p.n_sites = f.n_sites;
+  p.a_stride = f.a_stride;
+  p.c_stride = f.c_stride;
+  p.tile_sites = cfg.tile_sites;
+  p.stages = cfg.stages;
+  p.n_tiles = (int)((f.n_sites + cfg.tile_sites - 1) / cfg.tile_sites);
+  p.stage_bytes = (unsigned)(((long long)cfg.tile_sites * f.a_stride + 127) / 128 * 128);
+  p.out_bytes = kInPlace ? 0u : (unsigned)(((long long)cfg.tile_sites * 4 * NE_OUT * sizeof(V) + 127) / 128 * 128);
+  p.status = ctx.status;
+  p.b = make_b<A>(b);
+  const size_t smem = kSmemHeader + (size_t)p.stages * p.stage_bytes + (kInPlace ? 0 : 3 * (size_t)p.out_bytes);
+  if (smem > 227 * 1024) {
+    *ctx.err = "launch configuration needs " + std::to_string(smem) + " B of shared memory (max 232448)";
+    return SU3_ERR_INVALID_ARG;
+  }
+  auto kern = su3_aos_kernel<DT, NE_IN, ROWS_OUT>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return cuda_fail(ctx, "cudaFuncSetAttribute", e);
+  const int grid = (int)std::min<long long>(p.n_tiles, (long long)ctx.num_sms * cfg.ctas_per_sm);
+  kern<<<grid, cfg.block, smem, ctx.stream>>>(p);
+  e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, "su3_aos_kernel launch", e);
+  ++*ctx.launches;
+  return SU3_OK;
+}
+
+template <int DT, int NE_IN, int ROWS_OUT, int LAYOUT>
+static su3_status run_direct(const Form& f, const LaunchCfg& cfg, const void* a, const double* b, void* c,
+                             const LaunchCtx& ctx) {
+  using A = typename Storage<DT>::acc;
+  DirectArgs<A> p;
+  p.a = a;
+  p.c = c;
+  p.n_links = 4 * f.n_sites;
+  p.b = make_b<A>(b);
+  const int lpt = cfg.tile_sites;
+  const long long per_cta = (long long)cfg.block * lpt;
+  const int grid = (int)std::max<long long>(1, std::min<long long>((p.n_links + per_cta - 1) / per_cta,
+                                                                    (long long)ctx.num_sms * cfg.ctas_per_sm));
+  switch (lpt) {
+    case 1: su3_direct_kernel<DT, NE_IN, ROWS_OUT, LAYOUT, 1><<<grid, cfg.block, 0, ctx.stream>>>(p); break;
+    case 2: su3_direct_kernel<DT, NE_IN, ROWS_OUT, LAYOUT, 2><<<grid, cfg.block, 0, ctx.stream>>>(p); break;
+    case 4: su3_direct_kernel<DT, NE_IN, ROWS_OUT, LAYOUT, 4><<<grid, cfg.block, 0, ctx.stream>>>(p); break;
+    default:
+      *ctx.err = "links per thread (tile_sites) must be 1, 2 or 4 for SOA/AOSOA32";
+      return SU3_ERR_INVALID_ARG;
+  }
+  cudaError_t e = cudaGetLastError();
+  if (e != cudaSuccess) return cuda_fail(ctx, "su3_direct_kernel launch", e);
+  ++*ctx.launches;
+  return SU3_OK;
+}
+
+template <int DT, int NE_IN, int ROWS_OUT>
+static su3_status run_layout(const Form& f, const LaunchCfg& cfg, const void* a, const double* b, void* c,
+                             const LaunchCtx& ctx) {
+  switch (f.layout) {
+    case SU3_LAYOUT_AOS: return run_aos<DT, NE_IN, ROWS_OUT>(f, cfg, a, b, c, ctx);
+    case SU3_LAYOUT_AOSOA32: return run_direct<DT, NE_IN, ROWS_OUT, SU3_LAYOUT_AOSOA32>(f, cfg, a, b, c, ctx);
+    case SU3_LAYOUT_SOA: return run_direct<DT, NE_IN, ROWS_OUT, SU3_LAYOUT_SOA>(f, cfg, a, b, c, ctx);
+  }
+  return SU3_ERR_UNSUPPORTED;
+}
+
+template <int DT>
+static su3_status run_repr(const Form& f, const LaunchCfg& cfg, const void* a, const double* b, void* c,
+                           const LaunchCtx& ctx) {
+  if (f.repr_in == SU3_REPR_FULL18) return run_layout<DT, 9, 3>(f, cfg, a, b, c, ctx);
+  if (f.repr_out == SU3_REPR_TWOROW12) return run_layout<DT, 6, 2>(f, cfg, a, b, c, ctx);
+  return run_layout<DT, 6, 3>(f, cfg, a, b, c, ctx);
+}
+
+su3_status launch_mult(const Form& f, const LaunchCfg& cfg, const void* a, const double* b, void* c,
+                       const LaunchCtx& ctx) {
+  switch (f.dtype) {
+    case SU3_F64: return run_repr<kF64>(f, cfg, a, b, c, ctx);
+    case SU3_F32: return run_repr<kF32>(f, cfg, a, b, c, ctx);
+    case SU3_F16: return run_repr<kF16>(f, cfg, a, b, c, ctx);
+    case SU3_BF16: return run_repr<kBF16>(f, cfg, a, b, c, ctx);
+  }
+  return SU3_ERR_UNSUPPORTED;
+}
+
+}  // namespace su3

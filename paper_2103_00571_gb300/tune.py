@@ -1,0 +1,198 @@
+"""Autotuner for libsu3's launch configurations.
+
+For each form (dtype x repr x layout) it times su3_mult over a grid of launch configurations
+(block, tile_sites, stages, ctas_per_sm) on a lattice larger than L2, with CUDA events after
+warm-up, and keeps the fastest. The batched kernel's tile/block/stages are tuned the same way on
+the 96-lattice batch. Results go to ``tune_cache.json`` beside this file, keyed by GPU name and SM
+count, and ``apply_cached`` installs them on a handle (bench.py and the tests use the same).
+
+    python -m paper_2103_00571_gb300.tune [--L 48] [--forms all|f64-aos,...] [--batched]
+"""
+import argparse
+import itertools
+import json
+import os
+import time
+
+import numpy as np
+
+from . import _binding as B
+
+CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.json")
+
+DT = {"f64": B.F64, "f32": B.F32, "f16": B.F16, "bf16": B.BF16}
+RP = {"full": B.FULL18, "2row": B.TWOROW12}
+LY = {"aos": B.AOS, "aosoa32": B.AOSOA32, "soa": B.SOA}
+AR = {"native": B.NATIVE, "f32pair": B.F32PAIR}
+
+
+def form_name(desc):
+    inv = lambda m, v: [k for k, x in m.items() if x == v][0]  # noqa: E731
+    return "%s-%s-%s-%s" % (inv(DT, desc.dtype), inv(RP, desc.repr), inv(LY, desc.layout), inv(AR, desc.arith))
+
+
+def parse_form(name, n_sites=0):
+    d, r, l, a = (name.split("-") + ["native"])[:4]
+    return B.Desc(DT[d], RP[r], LY[l], n_sites, 0, AR[a])
+
+
+ALL_FORMS = ["f64-full-aos", "f32-full-aos", "f16-full-aos", "bf16-full-aos", "f64-2row-aos", "f32-2row-aos",
+             "f16-2row-aos", "f64-full-soa", "f32-full-soa", "f16-full-soa", "f64-full-aosoa32",
+             "f32-full-aosoa32", "f16-full-aosoa32", "bf16-full-aosoa32"]
+
+
+def gpu_key():
+    import torch
+    p = torch.cuda.get_device_properties(0)
+    return "%s/%d" % (p.name, p.multi_processor_count)
+
+
+def load_cache():
+    if not os.path.exists(CACHE):
+        return {}
+    with open(CACHE) as f:
+        return json.load(f)
+
+
+def apply_cached(h, key=None):
+    """Installs the cached configurations for this GPU on handle ``h``; returns what it applied."""
+    cache = load_cache()
+    key = key or gpu_key()
+    entry = cache.get(key, {})
+    for name, cfg in entry.get("forms", {}).items():
+        h.set_launch_cfg(parse_form(name), **cfg["cfg"])
+    if "batched" in entry:
+        h.set_batched_cfg(**entry["batched"]["cfg"])
+    return entry
+
+
+def candidates(desc):
+    if desc.layout == B.AOS:
+        site = B.link_bytes(desc.dtype, desc.repr) * 4
+        out = []
+        for block, tile_bytes, stages, cps in itertools.product((64, 128, 256), (9216, 18432, 36864),
+                                                                (3, 4, 6), (1, 2, 3)):
+            ts = max(8, tile_bytes // site)
+            smem = 1024 + stages * ((ts * site + 127) // 128 * 128)
+            if smem * cps > 227 * 1024:
+                continue
+            out.append(dict(block=block, tile_sites=ts, stages=stages, ctas_per_sm=cps))
+        return out
+    return [dict(block=bl, tile_sites=lpt, ctas_per_sm=c) for bl in (128, 256) for lpt in (1, 2, 4)
+            for c in (2, 4, 8)]
+
+
+def time_cfg(h, desc, abuf, b, cbuf, cfg, reps=5, iters=4):
+    import torch
+    h.set_launch_cfg(desc, **cfg)
+    s = torch.cuda.current_stream()
+    for _ in range(2):
+        h.mult(desc, abuf, b, desc, cbuf)
+    ts = []
+    for _ in range(reps):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(iters):
+            h.mult(desc, abuf, b, desc, cbuf)
+        e1.record(s)
+        e1.synchronize()
+        ts.append(e0.elapsed_time(e1) / iters)
+    h.sync()
+    return float(np.median(ts))
+
+
+def tune_forms(h, names, L=48, log=print):
+    import torch
+
+    import su3_inputs as gen
+    V = L ** 4
+    a64 = torch.from_numpy(gen.sites(gen.DEFAULT_SEED, 0, V)).cuda()
+    b = gen.bmat(gen.DEFAULT_SEED, 0, V)
+    results = {}
+    for name in names:
+        d = parse_form(name, V)
+        nb = B.array_bytes(d)
+        abuf = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        cbuf = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        h.pack(a64, d, abuf)
+        best = None
+        for cfg in candidates(d):
+            ms = time_cfg(h, d, abuf, b, cbuf, cfg)
+            if best is None or ms < best[0]:
+                best = (ms, cfg)
+        gbs = (B.link_bytes(d.dtype, d.repr) * 8 * V) / (best[0] * 1e-3) / 1e9
+        results[name] = {"cfg": best[1], "ms": round(best[0], 4), "GBps": round(gbs, 1), "L": L}
+        log("%-22s %s  %.3f ms  %.0f GB/s" % (name, best[1], best[0], gbs))
+        del abuf, cbuf
+    return results
+
+
+def tune_batched(h, log=print):
+    import ctypes
+
+    import torch
+
+    import su3_inputs as gen
+    ext = gen.extents(gen.DEFAULT_SEED, 96)
+    items, keep = [], []
+    for k in range(96):
+        V = int(np.prod(ext[k]))
+        dt = B.F64 if k % 2 == 0 else B.F32
+        d = B.Desc(dt, B.FULL18, B.AOS, V)
+        a = torch.from_numpy(gen.sites(gen.DEFAULT_SEED, k, V)).cuda()
+        abuf = torch.empty(B.array_bytes(d), dtype=torch.uint8, device="cuda")
+        h.pack(a, d, abuf)
+        cbuf = torch.empty_like(abuf)
+        keep += [abuf, cbuf]
+        items.append(B.BatchItem(d, abuf.data_ptr(), cbuf.data_ptr(),
+                                 (ctypes.c_double * 72)(*gen.bmat(gen.DEFAULT_SEED, k, V))))
+    best = None
+    for block, ts, stages, cps in itertools.product((128, 256), (16, 32, 64), (3, 4, 6), (1, 2, 3)):
+        if 1024 + stages * ((ts * 576 + 127) // 128 * 128) > 227 * 1024 // cps:
+            continue
+        cfg = dict(block=block, tile_sites=ts, stages=stages, ctas_per_sm=cps)
+        h.set_batched_cfg(**cfg)
+        for _ in range(3):
+            h.mult_batched(items, use_graph=True)
+        h.sync()
+        s = torch.cuda.current_stream()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        for _ in range(10):
+            h.mult_batched(items, use_graph=True)
+        e1.record(s)
+        e1.synchronize()
+        ms = e0.elapsed_time(e1) / 10
+        if best is None or ms < best[0]:
+            best = (ms, cfg)
+    h.set_batched_cfg(**best[1])
+    log("batched %s %.3f ms" % (best[1], best[0]))
+    return {"cfg": best[1], "ms": round(best[0], 4)}
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--L", type=int, default=48)
+    ap.add_argument("--forms", default="all")
+    ap.add_argument("--batched", action="store_true")
+    ap.add_argument("--out", default=CACHE)
+    args = ap.parse_args()
+    h = B.Handle(0)
+    names = ALL_FORMS if args.forms == "all" else args.forms.split(",")
+    cache = load_cache()
+    key = gpu_key()
+    entry = cache.get(key, {"forms": {}})
+    t0 = time.time()
+    entry["forms"].update(tune_forms(h, names, args.L))
+    if args.batched:
+        entry["batched"] = tune_batched(h)
+    entry["when"] = time.strftime("%Y-%m-%dT%H:%M:%SZ", time.gmtime())
+    cache[key] = entry
+    with open(args.out, "w") as f:
+        json.dump(cache, f, indent=1, sort_keys=True)
+    print("tuned %d forms in %.0f s -> %s" % (len(names), time.time() - t0, args.out))
+
+
+if __name__ == "__main__":
+    main()

@@ -1,0 +1,190 @@
+"""Edge cases and invariants of the CUDA path, all through the C ABI."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2103_00571_gb300 as su3
+import su3_inputs as gen
+from gpu_helpers import empty_bytes, run_form, to_dev
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def h():
+    return su3.Handle(0)
+
+
+def test_identity_b_bitwise(h):
+    V = 4099
+    a, _ = gen.lattice(1, V)
+    eye = np.zeros((4, 9, 2))
+    eye[:, [0, 4, 8], 0] = 1.0
+    got = run_form(h, a, eye.reshape(72), su3.F64)
+    assert np.array_equal(got.view(np.uint64), a.view(np.uint64))
+
+
+def test_paper_constant_case(h):
+    """a = 1+0i, b = 1/3+0i everywhere (the paper's initialisation) => c = 1+0i."""
+    a, b = gen.paper_constant(4096)
+    for dt, tl in ((su3.F64, 1e-15), (su3.F32, 1e-6), (su3.F16, 1e-3), (su3.BF16, 1e-2)):
+        got = run_form(h, a, b, dt).reshape(-1, 72)
+        assert np.max(np.abs(got[:, 0::2] - 1.0)) <= tl and np.max(np.abs(got[:, 1::2])) <= tl
+
+
+def test_iterations_are_idempotent(h):
+    """Each iteration recomputes c from the unchanged a: 10 iterations == 1, bit for bit."""
+    V = 5000
+    a, b = gen.lattice(2, V)
+    assert np.array_equal(run_form(h, a, b, su3.F64, iters=1), run_form(h, a, b, su3.F64, iters=10))
+
+
+def test_in_place(h):
+    import torch
+    V = 3001
+    a, b = gen.lattice(3, V)
+    for dt in (su3.F64, su3.F32):
+        d = su3.Desc(dt, su3.FULL18, su3.AOS, V)
+        buf = empty_bytes(su3.array_bytes(d))
+        h.pack(to_dev(a), d, buf)
+        h.mult(d, buf, b, d, buf)
+        out = torch.empty(V * 72, dtype=torch.float64, device="cuda")
+        h.unpack(d, buf, out)
+        h.sync()
+        ref = oracle.mult(a, b)
+        assert oracle.error(out.cpu().numpy(), ref)[0] <= (1e-13 if dt == su3.F64 else 2e-6)
+
+
+def test_stride_640_keeps_pads_and_canaries(h):
+    """The paper's padded 640-byte FP64 site: the kernel never writes bytes 576..639 of a site,
+    nor anything outside c (4 KiB canaries on both sides)."""
+    import torch
+    V = 2051
+    a, b = gen.lattice(4, V)
+    stride = 640
+    a640 = np.full((V, 80), -3.25)
+    a640[:, :72] = a.reshape(V, 72)
+    canary = 4096
+    d = su3.Desc(su3.F64, su3.FULL18, su3.AOS, V, stride)
+    cbig = torch.full((canary * 2 + V * stride,), 0xA5, dtype=torch.uint8, device="cuda")
+    cview_ptr = cbig.data_ptr() + canary
+    # pads of c pre-filled with a pattern
+    cbig[canary:canary + V * stride].view(torch.float64).view(V, 80)[:, 72:] = 9.5
+    a_dev = to_dev(a640.reshape(-1))
+    h.mult(d, a_dev, b, d, cview_ptr)
+    h.sync()
+    host = cbig.cpu().numpy()
+    assert np.all(host[:canary] == 0xA5) and np.all(host[-canary:] == 0xA5)
+    c = host[canary:canary + V * stride].view(np.float64).reshape(V, 80)
+    assert np.all(c[:, 72:] == 9.5)
+    assert oracle.error(c[:, :72].reshape(-1), oracle.mult(a, b))[0] <= 1e-13
+
+
+def test_canaries_packed(h):
+    import torch
+    V = 1237
+    a, b = gen.lattice(5, V)
+    for dt in (su3.F64, su3.F16):
+        d = su3.Desc(dt, su3.FULL18, su3.AOS, V)
+        n = su3.array_bytes(d)
+        abuf = empty_bytes(n)
+        h.pack(to_dev(a), d, abuf)
+        cbig = torch.full((n + 8192,), 0x5A, dtype=torch.uint8, device="cuda")
+        h.mult(d, abuf, b, d, cbig.data_ptr() + 4096)
+        h.sync()
+        host = cbig.cpu().numpy()
+        assert np.all(host[:4096] == 0x5A) and np.all(host[-4096:] == 0x5A)
+
+
+def test_empty_is_noop(h):
+    d = su3.Desc(su3.F64, su3.FULL18, su3.AOS, 0)
+    h.mult(d, 0, np.zeros(72), d, 0)
+    h.sync()
+
+
+def test_invalid_arguments_rejected(h):
+    V = 100
+    d = su3.Desc(su3.F64, su3.FULL18, su3.AOS, V)
+    buf = empty_bytes(su3.array_bytes(d) + 64)
+    b = np.zeros(72)
+    with pytest.raises(su3.Su3Error) as e:
+        h.mult(d, buf.data_ptr() + 8, b, d, buf.data_ptr() + 8)  # misaligned
+    assert e.value.status == 1
+    with pytest.raises(su3.Su3Error) as e:
+        h.mult(d, buf.data_ptr(), b, d, buf.data_ptr() + 16)  # partial overlap
+    assert e.value.status == 1
+    dc = su3.Desc(su3.F32, su3.FULL18, su3.AOS, V)
+    with pytest.raises(su3.Su3Error):
+        h.mult(d, buf.data_ptr(), b, dc, buf.data_ptr())  # dtype mismatch
+    with pytest.raises(su3.Su3Error):
+        h.mult(su3.Desc(su3.F64, su3.FULL18, su3.AOS, V, 600), buf.data_ptr(), b, None, buf.data_ptr())
+    with pytest.raises(su3.Su3Error):
+        h.set_launch_cfg(d, block=100)
+    h.sync()
+
+
+def test_launch_cfg_variants_agree():
+    """Every tile size / stage depth / block gives the same bits (sites are independent)."""
+    h = su3.Handle(0)  # its own handle: the configurations below stay local to it
+    V = 7000
+    a, b = gen.lattice(6, V)
+    for dt, lay in ((su3.F64, su3.AOS), (su3.F16, su3.AOS), (su3.F32, su3.SOA)):
+        base = run_form(h, a, b, dt, layout=lay)
+        cfgs = ({"tile_sites": 7, "stages": 2, "block": 64}, {"tile_sites": 64, "stages": 3, "block": 256},
+                {"tile_sites": 33, "stages": 8, "block": 128, "ctas_per_sm": 1})
+        if lay != su3.AOS:
+            cfgs = ({"tile_sites": 1, "block": 64}, {"tile_sites": 2, "block": 256}, {"tile_sites": 4, "ctas_per_sm": 1})
+        for cfg in cfgs:
+            assert np.array_equal(run_form(h, a, b, dt, layout=lay, cfg=cfg), base), (dt, cfg)
+    h.close()
+
+
+def test_host_path_matches_device_path(h):
+    import torch
+    V = 70001
+    a, b = gen.lattice(7, V)
+    d = su3.Desc(su3.F64, su3.FULL18, su3.AOS, V)
+    a_pin = torch.from_numpy(a).pin_memory()
+    c_pin = torch.empty(V * 72, dtype=torch.float64).pin_memory()
+    h.mult_host(d, a_pin.data_ptr(), b, d, c_pin.data_ptr())
+    dev = run_form(h, a, b, su3.F64)
+    assert np.array_equal(c_pin.numpy(), dev)
+    # pageable host memory and in place
+    a_page = a.copy()
+    h.mult_host(d, a_page, b, d, a_page)
+    assert np.array_equal(a_page, dev)
+
+
+def test_sync_host_deadline(h):
+    """A host deadline shorter than the queued work returns TIMEOUT; a later sync succeeds."""
+    import torch
+    V = 1 << 21
+    d = su3.Desc(su3.F64, su3.FULL18, su3.AOS, V)
+    buf = torch.zeros(su3.array_bytes(d), dtype=torch.uint8, device="cuda")
+    out = torch.empty_like(buf)
+    for _ in range(20):
+        h.mult(d, buf, np.zeros(72), d, out)
+    with pytest.raises(su3.Su3Error) as e:
+        h.sync(timeout_ms=0)
+    assert e.value.status == 5
+    h.sync()
+
+
+def test_device_bounded_wait_times_out_cleanly(h):
+    """The bounded mbarrier wait gives up, the status word reports TIMEOUT, the context lives on."""
+    h.selftest_wait_timeout(50)
+    with pytest.raises(su3.Su3Error) as e:
+        h.sync()
+    assert e.value.status == 5
+    h.sync()  # status word was cleared
+    V = 100
+    a, b = gen.lattice(8, V)
+    assert oracle.error(run_form(h, a, b, su3.F64), oracle.mult(a, b))[0] <= 1e-13
+
+
+def test_launch_count(h):
+    n0 = h.launch_count()
+    V = 100
+    a, b = gen.lattice(8, V)
+    run_form(h, a, b, su3.F64, iters=3)
+    assert h.launch_count() - n0 == 5  # pack + 3 mult + unpack

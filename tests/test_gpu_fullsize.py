@@ -1,0 +1,77 @@
+"""The benchmark's own sizes, in the launch configuration bench.py times (tuned or default):
+L=32 and L=48 compared element by element, L=64 on sampled sites the oracle recomputes one by one."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2103_00571_gb300 as su3
+import su3_inputs as gen
+from gpu_helpers import run_form, tol
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def h():
+    from paper_2103_00571_gb300 import tune
+    hd = su3.Handle(0)
+    tune.apply_cached(hd)
+    return hd
+
+
+def test_L32_f64_aos_full_compare(h):
+    V = 32 ** 4
+    a, b = gen.lattice(gen.DEFAULT_SEED, V)
+    got = run_form(h, a, b, su3.F64)
+    mx, rms = oracle.error(got, oracle.mult(a, b))
+    assert mx <= 1e-13, (mx, rms)
+
+
+@pytest.mark.parametrize("form", [(su3.F64, su3.FULL18, su3.AOS), (su3.F32, su3.FULL18, su3.AOS),
+                                  (su3.F64, su3.TWOROW12, su3.AOS), (su3.F32, su3.TWOROW12, su3.AOS),
+                                  (su3.F64, su3.FULL18, su3.SOA), (su3.F32, su3.FULL18, su3.SOA),
+                                  (su3.F64, su3.FULL18, su3.AOSOA32)],
+                         ids=["f64-aos", "f32-aos", "f64-2row-aos", "f32-2row-aos", "f64-soa", "f32-soa",
+                              "f64-aosoa32"])
+def test_L48_forms_full_compare(h, form, L48):
+    dt, rep, lay = form
+    a, b, ref = L48
+    got = run_form(h, a, b, dt, rep, rep, lay)
+    mx, rms = oracle.error(got, ref)
+    assert mx <= tol(dt, rep), (mx, rms)
+
+
+@pytest.fixture(scope="module")
+def L48():
+    V = 48 ** 4
+    a, b = gen.lattice(gen.DEFAULT_SEED, V)
+    return a, b, oracle.mult(a, b)
+
+
+@pytest.mark.parametrize("dtype", [su3.F64, su3.F16, su3.BF16, su3.F32])
+def test_L64_sampled(h, dtype):
+    """L=64 (16.7M sites): the whole lattice runs on the GPU; 65,536 random sites are recomputed by
+    the oracle from the same generator and compared element by element."""
+    import torch
+    V = 64 ** 4
+    a = gen.sites(gen.DEFAULT_SEED, 0, V)
+    b = gen.bmat(gen.DEFAULT_SEED, 0, V)
+    a_dev = torch.from_numpy(a).cuda()
+    del a
+    d = su3.Desc(dtype, su3.FULL18, su3.AOS, V)
+    if dtype == su3.F64:
+        abuf = a_dev
+    else:
+        abuf = torch.empty(su3.array_bytes(d), dtype=torch.uint8, device="cuda")
+        h.pack(a_dev, d, abuf)
+    cbuf = torch.empty(su3.array_bytes(d), dtype=torch.uint8, device="cuda")
+    h.mult(d, abuf, b, d, cbuf)
+    out = a_dev if dtype != su3.F64 else torch.empty_like(a_dev)
+    h.unpack(d, cbuf, out)
+    h.sync()
+    idx = np.sort(np.random.default_rng(64).choice(V, 65536, replace=False))
+    idx[0], idx[-1] = 0, V - 1  # both ends of the lattice
+    got = out.view(V, 72)[torch.from_numpy(idx).cuda()].cpu().numpy()
+    ref = oracle.mult_sites(gen.sites_at(gen.DEFAULT_SEED, 0, idx), b)
+    mx, rms = oracle.error(got, ref)
+    assert mx <= tol(dtype, su3.FULL18), (mx, rms)

@@ -1,0 +1,109 @@
+"""CUDA path vs the CPU FP64 oracle, element by element, for every form the library computes.
+
+Sizes span several tiles with ragged tails (tile = 32 sites for FP64 AoS, 64/128 for narrower
+forms; the direct kernels stride over 256-thread CTAs), plus the degenerate single site."""
+import numpy as np
+import pytest
+
+import oracle
+import paper_2103_00571_gb300 as su3
+import su3_inputs as gen
+from gpu_helpers import run_form, tol
+
+pytestmark = pytest.mark.gpu
+
+SIZES = [1, 4096, 4096 + 13, 3 * 8 ** 3 + 5]
+FORMS = [
+    (su3.F64, su3.FULL18, su3.FULL18),
+    (su3.F32, su3.FULL18, su3.FULL18),
+    (su3.F16, su3.FULL18, su3.FULL18),
+    (su3.BF16, su3.FULL18, su3.FULL18),
+    (su3.F64, su3.TWOROW12, su3.TWOROW12),
+    (su3.F32, su3.TWOROW12, su3.TWOROW12),
+    (su3.F64, su3.TWOROW12, su3.FULL18),
+    (su3.F32, su3.TWOROW12, su3.FULL18),
+    (su3.F16, su3.TWOROW12, su3.TWOROW12),
+    (su3.BF16, su3.TWOROW12, su3.FULL18),
+]
+LAYOUTS = [su3.AOS, su3.AOSOA32, su3.SOA]
+
+
+@pytest.fixture(scope="module")
+def h():
+    return su3.Handle(0)
+
+
+def _name(f):
+    return "%s-%s-%s" % ({0: "f64", 1: "f32", 2: "f16", 3: "bf16"}[f[0]], f[1], f[2])
+
+
+@pytest.mark.parametrize("layout", LAYOUTS, ids=["aos", "aosoa32", "soa"])
+@pytest.mark.parametrize("form", FORMS, ids=[_name(f) for f in FORMS])
+@pytest.mark.parametrize("V", SIZES)
+def test_form_vs_oracle(h, form, layout, V):
+    dtype, rin, rout = form
+    a, b = gen.lattice(gen.DEFAULT_SEED, V)
+    ref = oracle.mult(a, b)
+    got = run_form(h, a, b, dtype, rin, rout, layout)
+    mx, rms = oracle.error(got, ref)
+    assert mx <= tol(dtype, rin, rout), (mx, rms)
+
+
+@pytest.mark.parametrize("dtype", [su3.F64, su3.F32, su3.F16, su3.BF16])
+def test_error_also_vs_dequantised_input(h, dtype):
+    """Diagnostic split of the error: against the oracle run on the rounded (de-quantised) input the
+    remaining error is the arithmetic and output rounding alone, and must be no larger."""
+    V = 2000
+    a, b = gen.lattice(5, V)
+    got = run_form(h, a, b, dtype)
+    if dtype == su3.F64:
+        aq = a
+    elif dtype == su3.F32:
+        aq = oracle.round_float(a).astype(np.float64)
+    elif dtype == su3.F16:
+        aq = oracle.widen_half(oracle.round_half(a))
+    else:
+        aq = oracle.widen_bf16(oracle.round_bf16(a))
+    e_orig, _ = oracle.error(got, oracle.mult(a, b))
+    e_deq, _ = oracle.error(got, oracle.mult(aq, b))
+    assert e_deq <= e_orig * 1.0001 + 1e-15
+
+
+@pytest.mark.parametrize("dtype", [su3.F32, su3.F16, su3.BF16])
+@pytest.mark.parametrize("layout", LAYOUTS, ids=["aos", "aosoa32", "soa"])
+def test_pack_is_bit_exact(h, dtype, layout):
+    """su3_pack rounds once from FP64 to nearest even: the same bits as the oracle's rounding."""
+    import torch
+    V = 777
+    a, _ = gen.lattice(8, V)
+    d = su3.Desc(dtype, su3.FULL18, layout, V)
+    buf = torch.empty(su3.array_bytes(d), dtype=torch.uint8, device="cuda")
+    h.pack(torch.from_numpy(a).cuda(), d, buf)
+    back = torch.empty(V * 72, dtype=torch.float64, device="cuda")
+    h.unpack(d, buf, back)
+    h.sync()
+    back = back.cpu().numpy()
+    if dtype == su3.F32:
+        want = oracle.round_float(a).astype(np.float64)
+    elif dtype == su3.F16:
+        want = oracle.widen_half(oracle.round_half(a))
+    else:
+        want = oracle.widen_bf16(oracle.round_bf16(a))
+    assert np.array_equal(back, want)
+
+
+@pytest.mark.parametrize("layout", LAYOUTS, ids=["aos", "aosoa32", "soa"])
+def test_pack_unpack_roundtrip(h, layout):
+    """FP64 FULL18 round trip is bitwise; FP64 TWOROW12 rebuilds row 2 within 1e-15 (SU(3) input)."""
+    import torch
+    V = 999
+    a, _ = gen.lattice(9, V)
+    for rep, tol_rt in ((su3.FULL18, 0.0), (su3.TWOROW12, 1e-15)):
+        d = su3.Desc(su3.F64, rep, layout, V)
+        buf = torch.empty(su3.array_bytes(d), dtype=torch.uint8, device="cuda")
+        h.pack(torch.from_numpy(a).cuda(), d, buf)
+        back = torch.empty(V * 72, dtype=torch.float64, device="cuda")
+        h.unpack(d, buf, back)
+        h.sync()
+        err = np.max(np.abs(back.cpu().numpy() - a))
+        assert err <= tol_rt, (rep, err)
