@@ -57,6 +57,8 @@ def lib():
                 f = getattr(L, name)
                 f.argtypes = args
                 f.restype = None
+            L.su3o_threads.argtypes = []
+            L.su3o_threads.restype = ctypes.c_int
             _lib = L
     return _lib
 
@@ -159,6 +161,11 @@ def widen_bf16(h):
     out = np.empty(h.shape, dtype=np.float64)
     lib().su3o_widen_bf16(h.size, _ptr(h), _ptr(out))
     return out
+
+
+def threads():
+    """OpenMP threads the oracle's parallel loops use."""
+    return int(lib().su3o_threads())
 
 
 def error(x, ref):

@@ -271,3 +271,15 @@ void su3o_error(int64_t n, const double* x, const double* ref, double out[2]) {
   out[0] = mx;
   out[1] = n > 0 ? sqrt(ss / (double)n) : 0.0;
 }
+
+/* Number of OpenMP threads the parallel loops above use. */
+#ifdef _OPENMP
+#include <omp.h>
+#endif
+int su3o_threads(void) {
+#ifdef _OPENMP
+  return omp_get_max_threads();
+#else
+  return 1;
+#endif
+}
