@@ -144,6 +144,33 @@ su3_status su3_mult_host(su3_handle* h, const su3_desc* a_desc, const void* a_ho
 su3_status su3_mult_batched(su3_handle* h, int32_t n, const su3_batch_item* items, void* stream,
                             int32_t use_graph);
 
+/* Largest number of non-empty lattices one su3_mult_batched_static call accepts. */
+#define SU3_STATIC_MAX_LATTICES 256
+
+/*
+ * su3_mult_batched for callers that cannot allocate device memory. (The paper has no
+ * counterpart: this is a deployment convenience.) Some callers may not call cudaMalloc or
+ * cudaFree at all: plug-ins whose host application owns every device allocation through its own
+ * pool or fixed memory budget, and loops that must never stall, since cudaMalloc/cudaFree can
+ * synchronise the whole device. Those callers cannot create a handle either (su3_init allocates),
+ * so this entry point takes none and allocates nothing: the lattice descriptors go into a
+ * statically allocated device area of 256 + SU3_STATIC_MAX_LATTICES * 608 bytes (about 152 KB),
+ * which every GPU that loads libsu3 holds until the process exits.
+ *  - Runs on the calling thread's current CUDA device. The first call on each device looks up the
+ *    area's device address (set-up, once per device); make that first call before any stream
+ *    capture.
+ *  - Items follow su3_mult_batched's rules (F64 or F32, FULL18, packed AOS, NATIVE; a_dev/c_dev
+ *    caller-owned device buffers). More than SU3_STATIC_MAX_LATTICES non-empty items returns
+ *    SU3_ERR_INVALID_ARG before anything is enqueued.
+ *  - Synchronous: enqueues the descriptor upload and one kernel on `stream`, waits for `stream`,
+ *    and returns SU3_ERR_TIMEOUT if a device-side bounded wait ran out (the status word at the
+ *    start of the area, cleared at every call), SU3_ERR_CUDA on a CUDA error.
+ *  - Every call on a device shares the one area, which keeps the last call's descriptors: calls
+ *    that overlap on the GPU (e.g. from two host threads on different streams) race and must be
+ *    serialised by the caller.
+ */
+su3_status su3_mult_batched_static(int32_t n, const su3_batch_item* items, void* stream);
+
 /* ---- layout and precision conversion (outside the timed path) --------------------------- */
 
 /*

@@ -83,6 +83,7 @@ _SIGS = {
     "su3_set_launch_cfg": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Desc), ctypes.POINTER(LaunchCfg)]),
     "su3_get_launch_cfg": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Desc), ctypes.POINTER(LaunchCfg)]),
     "su3_launch_count": (ctypes.c_int64, [ctypes.c_void_p]),
+    "su3_mult_batched_static": (ctypes.c_int, [ctypes.c_int32, ctypes.POINTER(BatchItem), ctypes.c_void_p]),
     "su3_set_batched_cfg": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(LaunchCfg)]),
     "su3_get_batched_cfg": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(LaunchCfg)]),
     "su3_abi_version": (ctypes.c_int32, []),

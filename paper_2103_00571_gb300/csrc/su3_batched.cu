@@ -10,7 +10,10 @@
 // FP32 once per load).
 #include <cuda_runtime.h>
 
+#include <string.h>
+
 #include <algorithm>
+#include <mutex>
 
 #include "su3_device.cuh"
 #include "su3_internal.h"
@@ -200,3 +203,119 @@ su3_status launch_batched(const BatchDesc* descs_dev, int n, int total_tiles, co
 }
 
 }  // namespace su3
+
+// ---- su3_mult_batched_static: the batched launch without any device allocation -----------------
+//
+// The descriptor table and the status word live in a file-scope device array instead of handle
+// memory. Layout: bytes [0, 256) hold the status word (first 4 bytes), then up to
+// SU3_STATIC_MAX_LATTICES BatchDesc entries. Host code never uses the array's name as an address:
+// it asks the runtime for the device address once per device (cudaGetSymbolAddress, with that
+// device current) and passes that pointer to the kernel.
+
+namespace su3 {
+
+static_assert(sizeof(BatchDesc) == 608, "the static area's documented size assumes 608-byte descriptors");
+constexpr size_t kStaticHeader = 256;
+constexpr size_t kStaticBytes = kStaticHeader + (size_t)SU3_STATIC_MAX_LATTICES * sizeof(BatchDesc);
+
+static __device__ __align__(256) unsigned char g_su3_static_area[kStaticBytes];
+
+namespace {
+constexpr int kMaxDevices = 64;
+std::mutex g_static_mu;
+unsigned char* g_static_addr[kMaxDevices] = {};
+int g_static_sms[kMaxDevices] = {};
+}  // namespace
+
+// Device address of the static area on the current device (looked up once per device).
+static cudaError_t static_area(int dev, unsigned char** addr, int* sms) {
+  std::lock_guard<std::mutex> lock(g_static_mu);
+  if (!g_static_addr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_su3_static_area);
+    if (e != cudaSuccess) return e;
+    int n = 0;
+    e = cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return e;
+    g_static_addr[dev] = static_cast<unsigned char*>(p);
+    g_static_sms[dev] = n;
+  }
+  *addr = g_static_addr[dev];
+  *sms = g_static_sms[dev];
+  return cudaSuccess;
+}
+
+}  // namespace su3
+
+extern "C" su3_status su3_mult_batched_static(int32_t n, const su3_batch_item* items, void* stream) {
+  using namespace su3;
+  if (n < 0 || (n > 0 && !items)) return SU3_ERR_INVALID_ARG;
+  // validate everything and count tiles before touching the GPU
+  const BatchCfg cfg = default_batch_cfg();
+  int m = 0;
+  long long tiles = 0;
+  for (int i = 0; i < n; ++i) {
+    const su3_desc& d = items[i].desc;
+    if (su3_check_desc(&d) != SU3_OK) return SU3_ERR_INVALID_ARG;
+    if ((d.dtype != SU3_F64 && d.dtype != SU3_F32) || d.repr != SU3_REPR_FULL18 || d.layout != SU3_LAYOUT_AOS ||
+        d.arith != SU3_ARITH_NATIVE || (d.site_stride_bytes != 0 && d.site_stride_bytes != 4 * link_bytes(d.dtype, d.repr)))
+      return SU3_ERR_UNSUPPORTED;
+    if (d.n_sites == 0) continue;
+    const void* a = items[i].a_dev;
+    const void* c = items[i].c_dev;
+    if (!a || !c || ((uintptr_t)a & 15u) || ((uintptr_t)c & 15u)) return SU3_ERR_INVALID_ARG;
+    const uintptr_t nb = (uintptr_t)(d.n_sites * 4 * link_bytes(d.dtype, d.repr));
+    if (a != c && (uintptr_t)a < (uintptr_t)c + nb && (uintptr_t)c < (uintptr_t)a + nb) return SU3_ERR_INVALID_ARG;
+    ++m;
+    tiles += batch_tile_count(d.n_sites, cfg.tile_sites);
+  }
+  if (m > SU3_STATIC_MAX_LATTICES || tiles > (1ll << 30)) return SU3_ERR_INVALID_ARG;
+  if (m == 0) return SU3_OK;
+
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || dev < 0 || dev >= kMaxDevices) return SU3_ERR_CUDA;
+  unsigned char* area = nullptr;
+  int sms = 0;
+  if (static_area(dev, &area, &sms) != cudaSuccess) return SU3_ERR_CUDA;
+  cudaStream_t st = (cudaStream_t)stream;
+
+  // clear the status word, then upload the descriptors in small chunks from a stack buffer (each
+  // pageable-to-device copy has staged its source when it returns, so the buffer can be reused)
+  if (cudaMemsetAsync(area, 0, sizeof(unsigned), st) != cudaSuccess) return SU3_ERR_CUDA;
+  BatchDesc* table = reinterpret_cast<BatchDesc*>(area + kStaticHeader);
+  constexpr int kChunk = 16;
+  BatchDesc buf[kChunk];
+  int filled = 0, written = 0, first_tile = 0;
+  for (int i = 0; i < n; ++i) {
+    const su3_batch_item& it = items[i];
+    if (it.desc.n_sites == 0) continue;
+    BatchDesc& o = buf[filled++];
+    o.a = it.a_dev;
+    o.c = it.c_dev;
+    o.n_sites = it.desc.n_sites;
+    o.dtype = it.desc.dtype;
+    o.first_tile = first_tile;
+    memcpy(o.b, it.b, sizeof(o.b));
+    first_tile += batch_tile_count(it.desc.n_sites, cfg.tile_sites);
+    if (filled == kChunk || written + filled == m) {
+      if (cudaMemcpyAsync(table + written, buf, sizeof(BatchDesc) * filled, cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return SU3_ERR_CUDA;
+      written += filled;
+      filled = 0;
+    }
+  }
+  std::string err;
+  int64_t launches = 0;
+  LaunchCtx ctx;
+  ctx.stream = st;
+  ctx.status = reinterpret_cast<unsigned*>(area);
+  ctx.num_sms = sms;
+  ctx.launches = &launches;
+  ctx.err = &err;
+  su3_status s = launch_batched(table, m, first_tile, cfg, ctx);
+  if (s != SU3_OK) return s;
+  if (cudaStreamSynchronize(st) != cudaSuccess) return SU3_ERR_CUDA;
+  unsigned word = 0;
+  if (cudaMemcpy(&word, area, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return SU3_ERR_CUDA;
+  return word ? SU3_ERR_TIMEOUT : SU3_OK;
+}
