@@ -221,7 +221,8 @@ def source_digest():
 
 
 FORMS = [
-    # name, dtype, repr_in, repr_out, layout
+    # name, dtype, repr_in, repr_out, layout[, arith]
+    ("f64-f32pair-aos", 0, 0, 0, 0, 1), ("f64-f32pair-soa", 0, 0, 0, 2, 1), ("f64-f32pair-2row-aos", 0, 1, 1, 0, 1),
     ("f32-aos", 1, 0, 0, 0), ("f16-aos", 2, 0, 0, 0), ("bf16-aos", 3, 0, 0, 0),
     ("f64-2row-aos", 0, 1, 1, 0), ("f32-2row-aos", 1, 1, 1, 0), ("f16-2row-aos", 2, 1, 1, 0),
     ("f64-2row-to-full-aos", 0, 1, 0, 0),
@@ -335,9 +336,10 @@ def sample_error(torch, c_dev_f64, ref, V_sample):
 def forms_leg(h, torch, su3, a_dev, b, V, stream, f64_gbs, ref, V_sample, reps=10):
     out = {}
     f64_sups = f64_gbs * 1e9 / 1152.0
-    for name, dt, ri, ro, lay in FORMS:
-        da = su3.Desc(dt, ri, lay, V)
-        dc = su3.Desc(dt, ro, lay, V)
+    for name, dt, ri, ro, lay, *ar in FORMS:
+        arith = ar[0] if ar else 0
+        da = su3.Desc(dt, ri, lay, V, 0, arith)
+        dc = su3.Desc(dt, ro, lay, V, 0, arith)
         abuf = torch.empty(su3.array_bytes(da), dtype=torch.uint8, device=a_dev.device)
         cbuf = torch.empty(su3.array_bytes(dc), dtype=torch.uint8, device=a_dev.device)
         h.pack(a_dev, da, abuf, stream)

@@ -47,35 +47,29 @@ struct AosArgs {
 
 constexpr int kSmemHeader = 1024;  // mbarriers (<= 8 x 8 B) + b (<= 576 B), then 128-aligned data
 
-// Loads this thread's b[j] (j = tid % 4) into registers via shared memory.
-template <typename A>
-__device__ __forceinline__ void load_b_regs(const BMat<A>& b, A* bsh, A (&bre)[9], A (&bim)[9]) {
+// Stages b (72 reals) in shared memory and lets each thread's op take its direction j = tid % 4.
+template <class Op>
+__device__ __forceinline__ void load_b_op(const BMat<typename Op::BArg>& b, typename Op::BArg* bsh, Op& op) {
   for (int i = threadIdx.x; i < 72; i += blockDim.x) bsh[i] = b.v[i];
   __syncthreads();
-  const int j = threadIdx.x & 3;
-#pragma unroll
-  for (int e = 0; e < 9; ++e) {
-    bre[e] = bsh[18 * j + 2 * e];
-    bim[e] = bsh[18 * j + 2 * e + 1];
-  }
+  op.init(bsh + 18 * (threadIdx.x & 3));
 }
 
-// NE_IN complex elements per input link (9 full, 6 two-row); ROWS_OUT rows of c (3 or 2).
-// In place (ROWS_OUT*3 == NE_IN): the result overwrites the input tile in shared memory.
-// Otherwise (two-row in, full out) results go to a ring of 3 output buffers.
-template <int DT, int NE_IN, int ROWS_OUT>
-__global__ void __launch_bounds__(256) su3_aos_kernel(const __grid_constant__ AosArgs<typename Storage<DT>::acc> p) {
-  using S = Storage<DT>;
-  using A = typename S::acc;
-  using V = typename S::vec;
-  constexpr int NE_OUT = 3 * ROWS_OUT;
+// The AOS streaming kernel. Op::kNeIn complex elements per input link (9 full, 6 two-row),
+// Op::kNeOut per output link. In place (kNeOut == kNeIn): the result overwrites the input tile in
+// shared memory. Otherwise (two-row in, full out) results go to a ring of 3 output buffers.
+template <class Op>
+__global__ void __launch_bounds__(256) su3_aos_kernel(const __grid_constant__ AosArgs<typename Op::BArg> p) {
+  using V = typename Op::V;
+  using BA = typename Op::BArg;
+  constexpr int NE_IN = Op::kNeIn, NE_OUT = Op::kNeOut;
   constexpr bool kInPlace = (NE_OUT == NE_IN);
   constexpr int kLinkIn = NE_IN * (int)sizeof(V);
   constexpr int kLinkOut = NE_OUT * (int)sizeof(V);
 
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
-  A* bsh = reinterpret_cast<A*>(smem + 64);
+  BA* bsh = reinterpret_cast<BA*>(smem + 64);
   unsigned char* stage0 = smem + kSmemHeader;
   unsigned char* out0 = stage0 + (size_t)p.stages * p.stage_bytes;
 
@@ -85,8 +79,8 @@ __global__ void __launch_bounds__(256) su3_aos_kernel(const __grid_constant__ Ao
     for (int s = 0; s < S_; ++s) mbar_init(&full[s], 1);
     fence_mbar_init();
   }
-  A bre[9], bim[9];
-  load_b_regs(p.b, bsh, bre, bim);  // contains __syncthreads (also publishes the mbarrier init)
+  Op op;
+  load_b_op(p.b, bsh, op);  // contains __syncthreads (also publishes the mbarrier init)
 
   const uint64_t pol = policy_evict_first();
   const int my_tiles = p.n_tiles > (int)blockIdx.x ? (p.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
@@ -125,14 +119,8 @@ __global__ void __launch_bounds__(256) su3_aos_kernel(const __grid_constant__ Ao
       for (int q = tid; q < 4 * nt; q += blockDim.x) {
         const int site = q >> 2, j = q & 3;
         const V* src = reinterpret_cast<const V*>(in + (size_t)site * p.a_stride + j * kLinkIn);
-        Link<A> la, lc;
-#pragma unroll
-        for (int e = 0; e < NE_IN; ++e) S::unpack(src[e], la.re[e], la.im[e]);
-        if (NE_IN == 6 && ROWS_OUT == 3) rebuild_row2(la);
-        link_mult<ROWS_OUT>(la, bre, bim, lc);
         V* dst = kInPlace ? const_cast<V*>(src) : reinterpret_cast<V*>(out + (size_t)q * kLinkOut);
-#pragma unroll
-        for (int e = 0; e < NE_OUT; ++e) dst[e] = S::pack(lc.re[e], lc.im[e]);
+        op.apply(src, dst);
       }
     }
     fence_proxy_async_smem();
@@ -187,15 +175,13 @@ __device__ __forceinline__ long long elem_index(long long q, int e, long long n_
   return ((q >> 5) * NE + e) * 32 + (q & 31);  // AOSOA32
 }
 
-template <int DT, int NE_IN, int ROWS_OUT, int LAYOUT, int LPT>
-__global__ void __launch_bounds__(256) su3_direct_kernel(const __grid_constant__ DirectArgs<typename Storage<DT>::acc> p) {
-  using S = Storage<DT>;
-  using A = typename S::acc;
-  using V = typename S::vec;
-  constexpr int NE_OUT = 3 * ROWS_OUT;
-  __shared__ A bsh[72];
-  A bre[9], bim[9];
-  load_b_regs(p.b, bsh, bre, bim);
+template <class Op, int LAYOUT, int LPT>
+__global__ void __launch_bounds__(256) su3_direct_kernel(const __grid_constant__ DirectArgs<typename Op::BArg> p) {
+  using V = typename Op::V;
+  constexpr int NE_IN = Op::kNeIn, NE_OUT = Op::kNeOut;
+  __shared__ typename Op::BArg bsh[72];
+  Op op;
+  load_b_op(p.b, bsh, op);
   const V* a = reinterpret_cast<const V*>(p.a);
   V* c = reinterpret_cast<V*>(p.c);
   const long long T = (long long)gridDim.x * blockDim.x;  // a multiple of 4: j stays tid % 4
@@ -213,13 +199,10 @@ __global__ void __launch_bounds__(256) su3_direct_kernel(const __grid_constant__
     for (int u = 0; u < LPT; ++u) {
       const long long q = base + u * T;
       if (q < p.n_links) {
-        Link<A> la, lc;
+        V res[NE_OUT];
+        op.apply(buf[u], res);
 #pragma unroll
-        for (int e = 0; e < NE_IN; ++e) S::unpack(buf[u][e], la.re[e], la.im[e]);
-        if (NE_IN == 6 && ROWS_OUT == 3) rebuild_row2(la);
-        link_mult<ROWS_OUT>(la, bre, bim, lc);
-#pragma unroll
-        for (int e = 0; e < NE_OUT; ++e) stg_stream(c + elem_index<LAYOUT, NE_OUT>(q, e, p.n_links), S::pack(lc.re[e], lc.im[e]));
+        for (int e = 0; e < NE_OUT; ++e) stg_stream(c + elem_index<LAYOUT, NE_OUT>(q, e, p.n_links), res[e]);
       }
     }
   }
@@ -285,14 +268,13 @@ static su3_status cuda_fail(const LaunchCtx& ctx, const char* what, cudaError_t 
   return SU3_ERR_CUDA;
 }
 
-template <int DT, int NE_IN, int ROWS_OUT>
+template <class Op>
 static su3_status run_aos(const Form& f, const LaunchCfg& cfg, const void* a, const double* b, void* c,
                           const LaunchCtx& ctx) {
-  using A = typename Storage<DT>::acc;
-  using V = typename Storage<DT>::vec;
-  constexpr int NE_OUT = 3 * ROWS_OUT;
-  constexpr bool kInPlace = (NE_OUT == NE_IN);
-  AosArgs<A> p;
+  using BA = typename Op::BArg;
+  using V = typename Op::V;
+  constexpr bool kInPlace = (Op::kNeOut == Op::kNeIn);
+  AosArgs<BA> p;
   p.a = static_cast<const unsigned char*>(a);
   p.c = static_cast<unsigned char*>(c);
   p.n_sites = f.n_sites;
@@ -302,15 +284,16 @@ static su3_status run_aos(const Form& f, const LaunchCfg& cfg, const void* a, co
   p.stages = cfg.stages;
   p.n_tiles = (int)((f.n_sites + cfg.tile_sites - 1) / cfg.tile_sites);
   p.stage_bytes = (unsigned)(((long long)cfg.tile_sites * f.a_stride + 127) / 128 * 128);
-  p.out_bytes = kInPlace ? 0u : (unsigned)(((long long)cfg.tile_sites * 4 * NE_OUT * sizeof(V) + 127) / 128 * 128);
+  p.out_bytes =
+      kInPlace ? 0u : (unsigned)(((long long)cfg.tile_sites * 4 * Op::kNeOut * sizeof(V) + 127) / 128 * 128);
   p.status = ctx.status;
-  p.b = make_b<A>(b);
+  p.b = make_b<BA>(b);
   const size_t smem = kSmemHeader + (size_t)p.stages * p.stage_bytes + (kInPlace ? 0 : 3 * (size_t)p.out_bytes);
   if (smem > 227 * 1024) {
     *ctx.err = "launch configuration needs " + std::to_string(smem) + " B of shared memory (max 232448)";
     return SU3_ERR_INVALID_ARG;
   }
-  auto kern = su3_aos_kernel<DT, NE_IN, ROWS_OUT>;
+  auto kern = su3_aos_kernel<Op>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(ctx, "cudaFuncSetAttribute", e);
   const int grid = (int)std::min<long long>(p.n_tiles, (long long)ctx.num_sms * cfg.ctas_per_sm);
@@ -321,23 +304,22 @@ static su3_status run_aos(const Form& f, const LaunchCfg& cfg, const void* a, co
   return SU3_OK;
 }
 
-template <int DT, int NE_IN, int ROWS_OUT, int LAYOUT>
+template <class Op, int LAYOUT>
 static su3_status run_direct(const Form& f, const LaunchCfg& cfg, const void* a, const double* b, void* c,
                              const LaunchCtx& ctx) {
-  using A = typename Storage<DT>::acc;
-  DirectArgs<A> p;
+  DirectArgs<typename Op::BArg> p;
   p.a = a;
   p.c = c;
   p.n_links = 4 * f.n_sites;
-  p.b = make_b<A>(b);
+  p.b = make_b<typename Op::BArg>(b);
   const int lpt = cfg.tile_sites;
   const long long per_cta = (long long)cfg.block * lpt;
   const int grid = (int)std::max<long long>(1, std::min<long long>((p.n_links + per_cta - 1) / per_cta,
                                                                     (long long)ctx.num_sms * cfg.ctas_per_sm));
   switch (lpt) {
-    case 1: su3_direct_kernel<DT, NE_IN, ROWS_OUT, LAYOUT, 1><<<grid, cfg.block, 0, ctx.stream>>>(p); break;
-    case 2: su3_direct_kernel<DT, NE_IN, ROWS_OUT, LAYOUT, 2><<<grid, cfg.block, 0, ctx.stream>>>(p); break;
-    case 4: su3_direct_kernel<DT, NE_IN, ROWS_OUT, LAYOUT, 4><<<grid, cfg.block, 0, ctx.stream>>>(p); break;
+    case 1: su3_direct_kernel<Op, LAYOUT, 1><<<grid, cfg.block, 0, ctx.stream>>>(p); break;
+    case 2: su3_direct_kernel<Op, LAYOUT, 2><<<grid, cfg.block, 0, ctx.stream>>>(p); break;
+    case 4: su3_direct_kernel<Op, LAYOUT, 4><<<grid, cfg.block, 0, ctx.stream>>>(p); break;
     default:
       *ctx.err = "links per thread (tile_sites) must be 1, 2 or 4 for SOA/AOSOA32";
       return SU3_ERR_INVALID_ARG;
@@ -348,13 +330,13 @@ static su3_status run_direct(const Form& f, const LaunchCfg& cfg, const void* a,
   return SU3_OK;
 }
 
-template <int DT, int NE_IN, int ROWS_OUT>
+template <class Op>
 static su3_status run_layout(const Form& f, const LaunchCfg& cfg, const void* a, const double* b, void* c,
                              const LaunchCtx& ctx) {
   switch (f.layout) {
-    case SU3_LAYOUT_AOS: return run_aos<DT, NE_IN, ROWS_OUT>(f, cfg, a, b, c, ctx);
-    case SU3_LAYOUT_AOSOA32: return run_direct<DT, NE_IN, ROWS_OUT, SU3_LAYOUT_AOSOA32>(f, cfg, a, b, c, ctx);
-    case SU3_LAYOUT_SOA: return run_direct<DT, NE_IN, ROWS_OUT, SU3_LAYOUT_SOA>(f, cfg, a, b, c, ctx);
+    case SU3_LAYOUT_AOS: return run_aos<Op>(f, cfg, a, b, c, ctx);
+    case SU3_LAYOUT_AOSOA32: return run_direct<Op, SU3_LAYOUT_AOSOA32>(f, cfg, a, b, c, ctx);
+    case SU3_LAYOUT_SOA: return run_direct<Op, SU3_LAYOUT_SOA>(f, cfg, a, b, c, ctx);
   }
   return SU3_ERR_UNSUPPORTED;
 }
@@ -362,13 +344,20 @@ static su3_status run_layout(const Form& f, const LaunchCfg& cfg, const void* a,
 template <int DT>
 static su3_status run_repr(const Form& f, const LaunchCfg& cfg, const void* a, const double* b, void* c,
                            const LaunchCtx& ctx) {
-  if (f.repr_in == SU3_REPR_FULL18) return run_layout<DT, 9, 3>(f, cfg, a, b, c, ctx);
-  if (f.repr_out == SU3_REPR_TWOROW12) return run_layout<DT, 6, 2>(f, cfg, a, b, c, ctx);
-  return run_layout<DT, 6, 3>(f, cfg, a, b, c, ctx);
+  if (f.repr_in == SU3_REPR_FULL18) return run_layout<NativeOp<DT, 9, 3>>(f, cfg, a, b, c, ctx);
+  if (f.repr_out == SU3_REPR_TWOROW12) return run_layout<NativeOp<DT, 6, 2>>(f, cfg, a, b, c, ctx);
+  return run_layout<NativeOp<DT, 6, 3>>(f, cfg, a, b, c, ctx);
 }
 
 su3_status launch_mult(const Form& f, const LaunchCfg& cfg, const void* a, const double* b, void* c,
                        const LaunchCtx& ctx) {
+  if (f.arith == SU3_ARITH_F32PAIR) {
+    if (f.dtype != SU3_F64) return SU3_ERR_UNSUPPORTED;
+    if (f.repr_in == SU3_REPR_FULL18) return run_layout<PairF64Op<9, 3>>(f, cfg, a, b, c, ctx);
+    if (f.repr_out == SU3_REPR_TWOROW12) return run_layout<PairF64Op<6, 2>>(f, cfg, a, b, c, ctx);
+    *ctx.err = "F32PAIR arithmetic does not rebuild row 2 (TWOROW12 -> FULL18)";
+    return SU3_ERR_UNSUPPORTED;
+  }
   switch (f.dtype) {
     case SU3_F64: return run_repr<kF64>(f, cfg, a, b, c, ctx);
     case SU3_F32: return run_repr<kF32>(f, cfg, a, b, c, ctx);

@@ -40,14 +40,14 @@ def empty_bytes(n, fill=None):
 
 
 def run_form(h, a64, b, dtype, repr_in=su3.FULL18, repr_out=None, layout=su3.AOS, stride=0, cfg=None,
-             iters=1, stream=None):
+             iters=1, stream=None, arith=su3.NATIVE):
     """pack(a64) -> mult x iters -> unpack; returns the FP64 result as a numpy array [V*72]."""
     t = torch()
     repr_out = repr_in if repr_out is None else repr_out
     V = a64.size // 72
     a_src = to_dev(a64)
-    da = su3.Desc(dtype, repr_in, layout, V, stride)
-    dc = su3.Desc(dtype, repr_out, layout, V, stride)
+    da = su3.Desc(dtype, repr_in, layout, V, stride, arith)
+    dc = su3.Desc(dtype, repr_out, layout, V, stride, arith)
     abuf = empty_bytes(su3.array_bytes(da))
     cbuf = empty_bytes(su3.array_bytes(dc))
     h.pack(a_src, da, abuf, stream)

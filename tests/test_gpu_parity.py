@@ -107,3 +107,34 @@ def test_pack_unpack_roundtrip(h, layout):
         h.sync()
         err = np.max(np.abs(back.cpu().numpy() - a))
         assert err <= tol_rt, (rep, err)
+
+
+@pytest.mark.parametrize("layout", LAYOUTS, ids=["aos", "aosoa32", "soa"])
+@pytest.mark.parametrize("rep", [su3.FULL18, su3.TWOROW12], ids=["full", "2row"])
+@pytest.mark.parametrize("V", SIZES)
+def test_f32pair_vs_oracle(h, layout, rep, V):
+    """FP64 storage with FP32-pair arithmetic: within the FP64 tolerance of the oracle."""
+    a, b = gen.lattice(gen.DEFAULT_SEED, V)
+    ref = oracle.mult(a, b)
+    got = run_form(h, a, b, su3.F64, rep, rep, layout, arith=su3.F32PAIR)
+    mx, rms = oracle.error(got, ref)
+    assert mx <= tol(su3.F64, rep), (mx, rms)
+
+
+def test_f32pair_generic_and_constant_inputs(h):
+    """Non-SU(3) inputs of mixed magnitude (the relative bound scales with sum |a||b|) and the
+    paper's constant case, whose exact zeros the split replaces by values below 2^-73."""
+    rng = np.random.default_rng(4)
+    V = 3000
+    a = rng.standard_normal(V * 72) * np.exp(rng.uniform(-20, 20, V * 72))
+    _, b = gen.lattice(4, V)
+    got = run_form(h, a, b, su3.F64, arith=su3.F32PAIR)
+    ref = oracle.mult(a, b)
+    # sum over the six real terms of |x||y| <= sum_m (|re a|+|im a|)(|re b|+|im b|)
+    A = np.abs(a).reshape(V, 4, 3, 3, 2).sum(-1)
+    B = np.abs(b).reshape(4, 3, 3, 2).sum(-1)
+    bound = np.einsum("sjkm,jml->sjkl", A, B).repeat(2, axis=-1).reshape(-1)
+    assert np.all(np.abs(got - ref) <= 2.0 ** -42 * bound + 1e-30)
+    ac, bc = gen.paper_constant(4096)
+    got = run_form(h, ac, bc, su3.F64, arith=su3.F32PAIR).reshape(-1, 72)
+    assert np.max(np.abs(got[:, 0::2] - 1.0)) <= 1e-15 and np.max(np.abs(got[:, 1::2])) <= 1e-20
