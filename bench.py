@@ -41,6 +41,8 @@ def parse():
     ap.add_argument("--impl", default="native", choices=["native", "reference"])
     ap.add_argument("--L", type=int, default=64)
     ap.add_argument("--quick", action="store_true", help="headline only: no forms/batched/e2e/cpu legs")
+    ap.add_argument("--arith", default="native", choices=["native", "f32pair", "hybrid"],
+                    help="arithmetic of the FP64 AoS step (native = the plain FP64 method)")
     return ap.parse_args()
 
 
@@ -148,7 +150,18 @@ def cpu_baseline_leg(a_host, b, V_sample, min_seconds=10.0):
         if el >= min_seconds:
             break
     gbs = 1152.0 * V_sample * passes / el / 1e9
-    summary = {"value": round(gbs, 3), "unit": "GB/s", "cores": oracle.threads(), "kind": "oracle",
+    cores = oracle.threads()
+    # one core, shorter sample (the paper's strong-scaling baseline point)
+    oracle.set_threads(1)
+    t1 = time.perf_counter()
+    n1 = 0
+    while time.perf_counter() - t1 < 2.0:
+        oracle.mult(a[: 65536 * 72], b)
+        n1 += 1
+    el1 = time.perf_counter() - t1
+    oracle.set_threads(cores)
+    summary = {"value": round(gbs, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
+               "one_core_GBps": round(1152.0 * 65536 * n1 / el1 / 1e9, 3),
                "site_updates_per_s": round(V_sample * passes / el, 1),
                "sample": "%d sites (the first %d of the L=64 lattice) x %d passes, %.1f s, FP64, plain C "
                          "OpenMP loop over sites (the paper's VersionX form)" % (V_sample, V_sample, passes, el)}
@@ -222,7 +235,8 @@ def source_digest():
 
 FORMS = [
     # name, dtype, repr_in, repr_out, layout[, arith]
-    ("f64-f32pair-aos", 0, 0, 0, 0, 1), ("f64-f32pair-soa", 0, 0, 0, 2, 1), ("f64-f32pair-2row-aos", 0, 1, 1, 0, 1),
+    ("f64-hybrid-aos", 0, 0, 0, 0, 2), ("f64-hybrid-aosoa32", 0, 0, 0, 1, 2), ("f64-hybrid-2row-aos", 0, 1, 1, 0, 2),
+    ("f64-f32pair-aos", 0, 0, 0, 0, 1), ("f64-f32pair-aosoa32", 0, 0, 0, 1, 1), ("f64-f32pair-2row-aos", 0, 1, 1, 0, 1),
     ("f32-aos", 1, 0, 0, 0), ("f16-aos", 2, 0, 0, 0), ("bf16-aos", 3, 0, 0, 0),
     ("f64-2row-aos", 0, 1, 1, 0), ("f32-2row-aos", 1, 1, 1, 0), ("f16-2row-aos", 2, 1, 1, 0),
     ("f64-2row-to-full-aos", 0, 1, 0, 0),
@@ -254,7 +268,8 @@ def run_native(args, world, rank, local):
     b = gen.bmat(SEED, rank, V)
     a_dev = a_host.to(dev)
     c_dev = torch.empty_like(a_dev)
-    d64 = su3.Desc(su3.F64, su3.FULL18, su3.AOS, V)
+    arith = {"native": su3.NATIVE, "f32pair": su3.F32PAIR, "hybrid": su3.HYBRID}[args.arith]
+    d64 = su3.Desc(su3.F64, su3.FULL18, su3.AOS, V, 0, arith)
     step = lambda: h.mult(d64, a_dev, b, d64, c_dev, stream)  # noqa: E731
 
     for _ in range(args.warmup):
@@ -283,19 +298,28 @@ def run_native(args, world, rank, local):
     traffic = None
     if tr and tr.get("source_digest") == source_digest():
         traffic = tr["bytes_per_site"] * V
-    roofline = {"bound": "alu", "achieved": round(achieved_tf, 4), "peak": round(fp64_peak, 4),
-                "unit": "TFLOP/s", "frac": round(achieved_tf / fp64_peak, 4), "traffic": traffic,
-                "kernel": "su3_aos_kernel<F64,9,3>",
-                "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x %.0f MHz (max SM clock)" % sm_max,
-                "hbm": {"achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
-                        "frac": round(achieved_gbs / hbm_peak, 4), "peak_source": peak_src + " hbm_gbs"}}
+    hbm_roof = {"achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
+                "frac": round(achieved_gbs / hbm_peak, 4), "peak_source": peak_src + " hbm_gbs"}
+    if args.arith == "native":
+        roofline = {"bound": "alu", "achieved": round(achieved_tf, 4), "peak": round(fp64_peak, 4),
+                    "unit": "TFLOP/s", "frac": round(achieved_tf / fp64_peak, 4), "traffic": traffic,
+                    "kernel": "su3_aos_kernel<NativeOp<F64,9,3>>",
+                    "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x %.0f MHz (max SM clock)" % sm_max,
+                    "hbm": hbm_roof}
+    else:
+        tr = traffic_record().get("su3_aos_kernel<f64,full,%s>" % args.arith, {})
+        traffic = tr["bytes_per_site"] * V if tr and tr.get("source_digest") == source_digest() else None
+        roofline = dict(hbm_roof, bound="hbm", traffic=traffic,
+                        kernel="su3_aos_kernel<%s<9,3>>" % ("PairF64Op" if args.arith == "f32pair" else "HybridF64Op"))
 
     line = {"metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "scaling": "weak", "vs_baseline": None,
+            "dtype": {"native": "f64", "f32pair": "f32x2 (FP64 storage)", "hybrid": "f64 + f32x2"}[args.arith],
+            "data": "synthetic",
             "config": {"workload": "L=64 FP64 AoS SU3_Bench link multiply (c[i][j] = a[i][j] x b[j], "
                                    "%d sites, 576 B read + 576 B written per site)" % V,
-                       "lattice": "%d^4" % L, "form": "f64-full18-aos", "seed": SEED,
+                       "lattice": "%d^4" % L, "form": "f64-full18-aos-" + args.arith, "seed": SEED,
                        "inputs": "random SU(3) (Gram-Schmidt on Gaussian rows), one lattice per GPU",
                        "l2": "inputs larger than L2 (%.1f GB touched per step vs 129 MB L2): no flush"
                              % (bytes_per_step / 1e9),
@@ -312,8 +336,9 @@ def run_native(args, world, rank, local):
         line["cpu_baseline"] = cpu
         # speedup at error of every form on the same lattice
         line["forms"] = forms_leg(h, torch, su3, a_dev, b, V, stream, value, ref, V_sample)
+        line["paper_site640"] = site640_leg(h, torch, su3, a_dev, b, V, stream, ref, V_sample)
         fp64_err = sample_error(torch, c_dev, ref, V_sample)
-        line["forms"]["f64-aos"] = {"GBps": round(value / world, 1), "site_updates_per_s": round(sups / world, 1),
+        line["forms"]["f64-aos-" + args.arith] = {"GBps": round(value / world, 1), "site_updates_per_s": round(sups / world, 1),
                                     "speedup_vs_f64": 1.0, "max_err": fp64_err[0], "rms_err": fp64_err[1],
                                     "tol": 1e-13, "ok": fp64_err[0] <= 1e-13}
     if not args.quick:
@@ -369,6 +394,35 @@ def forms_leg(h, torch, su3, a_dev, b, V, stream, f64_gbs, ref, V_sample, reps=1
         del abuf, cbuf, c64
         torch.cuda.empty_cache()
     return out
+
+
+def site640_leg(h, torch, su3, a_dev, b, V, stream, ref, V_sample, reps=10):
+    """The paper's own FP64 Site: 4 links plus coordinates, index, parity and padding to 640 bytes
+    (§Background), so a site update moves 2 x 640 B by the paper's accounting while the kernel
+    reads 640 B (pads included, in whole bulk copies) and writes only the 576 link bytes per site."""
+    d = su3.Desc(su3.F64, su3.FULL18, su3.AOS, V, 640)
+    abuf = torch.empty(su3.array_bytes(d), dtype=torch.uint8, device=a_dev.device)
+    cbuf = torch.zeros_like(abuf)
+    h.pack(a_dev, d, abuf, stream)
+    res = {}
+    for arith, name in ((su3.NATIVE, "native"), (su3.F32PAIR, "f32pair")):
+        dd = su3.Desc(su3.F64, su3.FULL18, su3.AOS, V, 640, arith)
+        fn = lambda: h.mult(dd, abuf, b, dd, cbuf, stream)  # noqa: E731
+        for _ in range(3):
+            fn()
+        h.sync(stream)
+        _, per = time_launches(h, torch, fn, reps, stream)
+        sups = V / (per * 1e-3)
+        c64 = torch.empty(V_sample * 72, dtype=torch.float64, device=a_dev.device)
+        h.unpack(su3.Desc(su3.F64, su3.FULL18, su3.AOS, V_sample, 640), cbuf, c64, stream)
+        h.sync(stream)
+        err = sample_error(torch, c64, ref, V_sample)
+        res[name] = {"site_updates_per_s": round(sups, 1), "paper_GBps_2x640B": round(1280 * sups / 1e9, 1),
+                     "link_GBps_1152B": round(1152 * sups / 1e9, 1), "ms": round(per, 4), "max_err": err[0],
+                     "tol": 1e-13, "ok": err[0] <= 1e-13}
+    del abuf, cbuf
+    torch.cuda.empty_cache()
+    return res
 
 
 def e2e_leg(h, torch, su3, a_host, b, V, args, stream, world, dev):

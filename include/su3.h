@@ -72,9 +72,16 @@ typedef enum { SU3_LAYOUT_AOS = 0, SU3_LAYOUT_AOSOA32 = 1, SU3_LAYOUT_SOA = 2 } 
  * sum_m |a[k][m]||b[m][l]| per output (measured max 3e-14 against the FP64 oracle on SU(3)
  * data, whose entries are <= 1). Valid for finite inputs with |x| < 2^127; input magnitudes below
  * 2^-74 (including zeros) act as values below 2^-73. Supported reprs: FULL18 -> FULL18 and
- * TWOROW12 -> TWOROW12. Must be NATIVE for F32/F16/BF16 storage and for batched items.
+ * TWOROW12 -> TWOROW12. Must be NATIVE for F32/F16/BF16 storage and for batched items
+ * (HYBRID, below, likewise).
  */
-typedef enum { SU3_ARITH_NATIVE = 0, SU3_ARITH_F32PAIR = 1 } su3_arith;
+typedef enum { SU3_ARITH_NATIVE = 0, SU3_ARITH_F32PAIR = 1, SU3_ARITH_HYBRID = 2 } su3_arith;
+/*
+ * SU3_ARITH_HYBRID (F64 storage): in every CTA the first round(native_permille/1000 * warps) warps
+ * compute their links with NATIVE FP64 FMAs on the FP64 pipe while the other warps use F32PAIR on
+ * the FP32 pipe, so both pipes work at once. Each link's result is exactly what NATIVE or F32PAIR
+ * would produce for it; accuracy is that of F32PAIR. Same repr and range rules as F32PAIR.
+ */
 
 typedef struct {
   int32_t dtype;              /* su3_dtype */
@@ -94,6 +101,7 @@ typedef struct {
   int32_t tile_sites;   /* AOS: sites per shared-memory tile; others: links per thread x 32 */
   int32_t stages;       /* AOS: shared-memory pipeline depth (2..8) */
   int32_t ctas_per_sm;  /* CTAs per SM in the persistent grid */
+  int32_t native_permille;  /* HYBRID only: share of each CTA's warps computing natively, 1/1000 */
 } su3_launch_cfg;
 
 /* One lattice of a batched call. a/c are device pointers; b as in su3_mult. */

@@ -59,6 +59,8 @@ def lib():
                 f.restype = None
             L.su3o_threads.argtypes = []
             L.su3o_threads.restype = ctypes.c_int
+            L.su3o_set_threads.argtypes = [ctypes.c_int]
+            L.su3o_set_threads.restype = None
             _lib = L
     return _lib
 
@@ -166,6 +168,11 @@ def widen_bf16(h):
 def threads():
     """OpenMP threads the oracle's parallel loops use."""
     return int(lib().su3o_threads())
+
+
+def set_threads(n):
+    """Sets the OpenMP thread count of the oracle's parallel loops."""
+    lib().su3o_set_threads(int(n))
 
 
 def error(x, ref):

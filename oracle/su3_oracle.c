@@ -283,3 +283,12 @@ int su3o_threads(void) {
   return 1;
 #endif
 }
+
+/* Sets the number of OpenMP threads of the parallel loops above (for single-core timing). */
+void su3o_set_threads(int n) {
+#ifdef _OPENMP
+  if (n > 0) omp_set_num_threads(n);
+#else
+  (void)n;
+#endif
+}

@@ -16,7 +16,7 @@ from . import build as _build
 F64, F32, F16, BF16 = 0, 1, 2, 3
 FULL18, TWOROW12 = 0, 1
 AOS, AOSOA32, SOA = 0, 1, 2
-NATIVE, F32PAIR = 0, 1
+NATIVE, F32PAIR, HYBRID = 0, 1, 2
 
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_NOT_INITIALIZED, ERR_TIMEOUT, ERR_FAULT_INJECTED = range(7)
 
@@ -47,7 +47,7 @@ class Desc(ctypes.Structure):
 
 class LaunchCfg(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32), ("tile_sites", ctypes.c_int32), ("stages", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("native_permille", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -217,7 +217,8 @@ class Handle:
         self._check(lib().su3_sync(self._h, _stream_ptr(stream), timeout_ms), "su3_sync")
 
     def set_launch_cfg(self, form, **cfg):
-        c = LaunchCfg(cfg.get("block", 0), cfg.get("tile_sites", 0), cfg.get("stages", 0), cfg.get("ctas_per_sm", 0))
+        c = LaunchCfg(cfg.get("block", 0), cfg.get("tile_sites", 0), cfg.get("stages", 0), cfg.get("ctas_per_sm", 0),
+                      cfg.get("native_permille", 0))
         self._check(lib().su3_set_launch_cfg(self._h, ctypes.byref(form), ctypes.byref(c)), "su3_set_launch_cfg")
 
     def get_launch_cfg(self, form):

@@ -106,6 +106,8 @@ su3_status check_cfg(su3_handle* h, const Form& f, const LaunchCfg& c) {
   if (c.block < 32 || c.block > 256 || c.block % 32)
     return fail(h, SU3_ERR_INVALID_ARG, "block must be a multiple of 32 in [32, 256]");
   if (c.ctas_per_sm < 1 || c.ctas_per_sm > 32) return fail(h, SU3_ERR_INVALID_ARG, "ctas_per_sm must be in [1, 32]");
+  if (c.native_permille < 0 || c.native_permille > 1000)
+    return fail(h, SU3_ERR_INVALID_ARG, "native_permille must be in [0, 1000]");
   if (f.layout == SU3_LAYOUT_AOS) {
     if (c.stages < 2 || c.stages > 8) return fail(h, SU3_ERR_INVALID_ARG, "stages must be in [2, 8]");
     if (c.tile_sites < 1 || c.tile_sites > 1024) return fail(h, SU3_ERR_INVALID_ARG, "tile_sites must be in [1, 1024]");
@@ -133,7 +135,7 @@ su3_status make_form(su3_handle* h, const su3_desc* ad, const su3_desc* cd, Form
     return fail(h, SU3_ERR_INVALID_ARG, "a and c must share dtype, layout, arith and n_sites");
   if (ad->repr == SU3_REPR_FULL18 && cd->repr != SU3_REPR_FULL18)
     return fail(h, SU3_ERR_UNSUPPORTED, "FULL18 input needs FULL18 output");
-  if (ad->arith == SU3_ARITH_F32PAIR && ad->repr == SU3_REPR_TWOROW12 && cd->repr == SU3_REPR_FULL18)
+  if (ad->arith != SU3_ARITH_NATIVE && ad->repr == SU3_REPR_TWOROW12 && cd->repr == SU3_REPR_FULL18)
     return fail(h, SU3_ERR_UNSUPPORTED, "F32PAIR arithmetic does not rebuild row 2 (TWOROW12 -> FULL18)");
   f->dtype = ad->dtype;
   f->repr_in = ad->repr;
@@ -184,8 +186,8 @@ su3_status su3_check_desc(const su3_desc* d) {
   if (d->dtype < SU3_F64 || d->dtype > SU3_BF16) return SU3_ERR_INVALID_ARG;
   if (d->repr < SU3_REPR_FULL18 || d->repr > SU3_REPR_TWOROW12) return SU3_ERR_INVALID_ARG;
   if (d->layout < SU3_LAYOUT_AOS || d->layout > SU3_LAYOUT_SOA) return SU3_ERR_INVALID_ARG;
-  if (d->arith < SU3_ARITH_NATIVE || d->arith > SU3_ARITH_F32PAIR) return SU3_ERR_INVALID_ARG;
-  if (d->arith == SU3_ARITH_F32PAIR && d->dtype != SU3_F64) return SU3_ERR_INVALID_ARG;
+  if (d->arith < SU3_ARITH_NATIVE || d->arith > SU3_ARITH_HYBRID) return SU3_ERR_INVALID_ARG;
+  if (d->arith != SU3_ARITH_NATIVE && d->dtype != SU3_F64) return SU3_ERR_INVALID_ARG;
   if (d->n_sites < 0 || d->n_sites > ((int64_t)1 << 36)) return SU3_ERR_INVALID_ARG;
   const int64_t lb = link_bytes(d->dtype, d->repr);
   if (d->layout == SU3_LAYOUT_AOS) {
@@ -274,6 +276,7 @@ su3_status su3_set_launch_cfg(su3_handle* h, const su3_desc* form, const su3_lau
   if (cfg->tile_sites) c.tile_sites = cfg->tile_sites;
   if (cfg->stages) c.stages = cfg->stages;
   if (cfg->ctas_per_sm) c.ctas_per_sm = cfg->ctas_per_sm;
+  if (cfg->native_permille) c.native_permille = cfg->native_permille;
   su3_status s = check_cfg(h, f, c);
   if (s != SU3_OK) return s;
   h->cfgs[form_key(form)] = c;
@@ -294,6 +297,7 @@ su3_status su3_get_launch_cfg(su3_handle* h, const su3_desc* form, su3_launch_cf
   cfg->tile_sites = c.tile_sites;
   cfg->stages = c.stages;
   cfg->ctas_per_sm = c.ctas_per_sm;
+  cfg->native_permille = c.native_permille;
   return SU3_OK;
 }
 
@@ -321,6 +325,7 @@ su3_status su3_get_batched_cfg(su3_handle* h, su3_launch_cfg* cfg) {
   cfg->tile_sites = h->bcfg.tile_sites;
   cfg->stages = h->bcfg.stages;
   cfg->ctas_per_sm = h->bcfg.ctas_per_sm;
+  cfg->native_permille = 0;
   return SU3_OK;
 }
 
@@ -456,9 +461,9 @@ su3_status su3_mult_host(su3_handle* h, const su3_desc* a_desc, const void* a_ho
     e = cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_err(h, "cudaEventCreate", e);
   }
-  // chunks of whole sites, a multiple of the kernel tile, ~64 MB of input each
+  // chunks of whole sites, a multiple of the kernel tile, ~256 MB of input each
   const int64_t a_site = f.a_stride, c_site = f.c_stride;
-  int64_t chunk = std::max<int64_t>(cfg.tile_sites, (64ll << 20) / a_site / cfg.tile_sites * cfg.tile_sites);
+  int64_t chunk = std::max<int64_t>(cfg.tile_sites, (256ll << 20) / a_site / cfg.tile_sites * cfg.tile_sites);
   chunk = std::min<int64_t>(chunk, f.n_sites);
   const size_t a_bytes = (size_t)(chunk * a_site), c_bytes = (size_t)(chunk * c_site);
   const size_t need = (a_bytes + 255) / 256 * 256 + c_bytes;

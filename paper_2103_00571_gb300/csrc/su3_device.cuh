@@ -257,7 +257,8 @@ struct NativeOp {
   using BArg = A;              // precision of b in the kernel parameters
   static constexpr int kNeIn = NE_IN, kNeOut = 3 * ROWS_OUT;
   A bre[9], bim[9];
-  __device__ __forceinline__ void init(const BArg* bj) {
+  __device__ __forceinline__ void begin_tile(int) {}
+  __device__ __forceinline__ void init(const BArg* bj, int /*native_warps*/) {
 #pragma unroll
     for (int e = 0; e < 9; ++e) {
       bre[e] = bj[2 * e];
@@ -315,27 +316,29 @@ __device__ __forceinline__ double f32_bits_to_f64(float f) {
 }
 
 // sum_{t<6} x_t * y_t for pairs x = (xh, xl) (sign already folded in) and y = (yh, yl).
+// The error terms go to three independent accumulators (TwoSum errors, product errors, cross
+// products) so that no dependency chain is longer than two operations per term.
 __device__ __forceinline__ double dot6_pair(const float (&xh)[6], const float (&xl)[6], const float (&yh)[6],
                                             const float (&yl)[6]) {
   float s = xh[0] * yh[0];
-  float L = fmaf(xh[0], yh[0], -s);
-  L = fmaf(xh[0], yl[0], L);
-  L = fmaf(xl[0], yh[0], L);
+  float Le = fmaf(xh[0], yh[0], -s);
+  float Lc = fmaf(xh[0], yl[0], xl[0] * yh[0]);
+  float Lt = 0.0f;
 #pragma unroll
   for (int t = 1; t < 6; ++t) {
     const float p = xh[t] * yh[t];
-    const float e = fmaf(xh[t], yh[t], -p);
     const float s2 = s + p;
     const float z = s2 - s;
     const float t1 = s - (s2 - z);
     const float t2 = p - z;
     s = s2;
-    L = L + t1;
-    L = L + t2;
-    L = L + e;
-    L = fmaf(xh[t], yl[t], L);
-    L = fmaf(xl[t], yh[t], L);
+    Lt = Lt + t1;
+    Lt = Lt + t2;
+    Le = Le + fmaf(xh[t], yh[t], -p);
+    Lc = fmaf(xh[t], yl[t], Lc);
+    Lc = fmaf(xl[t], yh[t], Lc);
   }
+  const float L = (Lt + Le) + Lc;
   return f32_bits_to_f64(s) + f32_bits_to_f64(L);
 }
 
@@ -346,7 +349,8 @@ struct PairF64Op {
   static constexpr int kNeIn = NE_IN, kNeOut = 3 * ROWS_OUT;
   // b[j] split once per thread: (hi, lo) of every real, [m][l] order
   float brh[9], brl[9], bih[9], bil[9];
-  __device__ __forceinline__ void init(const double* bj) {
+  __device__ __forceinline__ void begin_tile(int) {}
+  __device__ __forceinline__ void init(const double* bj, int /*native_warps*/) {
 #pragma unroll
     for (int e = 0; e < 9; ++e) {
       const double r = bj[2 * e], i = bj[2 * e + 1];
@@ -399,6 +403,34 @@ struct PairF64Op {
         dst[3 * k + l] = make_double2(re, im);
       }
     }
+  }
+};
+
+// HYBRID: per tile, warp w uses the FP64 pipe (NATIVE) when (tile + w) % period == 0 and FP32
+// pairs otherwise, period = warps / native_warps. The native work rotates over all warps, so it
+// is spread over every SM sub-partition's FP64 unit. Each thread keeps both forms of its b[j].
+template <int NE_IN, int ROWS_OUT>
+struct HybridF64Op {
+  using V = double2;
+  using BArg = double;
+  static constexpr int kNeIn = NE_IN, kNeOut = 3 * ROWS_OUT;
+  NativeOp<kF64, NE_IN, ROWS_OUT> nat;
+  PairF64Op<NE_IN, ROWS_OUT> pair;
+  int period;  // 0: never native
+  bool native;
+  __device__ __forceinline__ void init(const double* bj, int native_warps) {
+    nat.init(bj, 0);
+    pair.init(bj, 0);
+    const int warps = (int)(blockDim.x >> 5);
+    period = native_warps > 0 ? max(1, warps / native_warps) : 0;
+    native = false;
+  }
+  __device__ __forceinline__ void begin_tile(int k) {
+    native = period > 0 && ((k + (int)(threadIdx.x >> 5)) % period) == 0;
+  }
+  __device__ __forceinline__ void apply(const V* src, V* dst) const {
+    if (native) nat.apply(src, dst);
+    else pair.apply(src, dst);
   }
 };
 

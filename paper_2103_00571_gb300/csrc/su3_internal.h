@@ -29,6 +29,7 @@ struct LaunchCfg {
   int tile_sites;
   int stages;
   int ctas_per_sm;
+  int native_permille;  // HYBRID: share of tiles on the FP64 pipe
 };
 
 // Everything a launcher needs from the handle.

@@ -41,6 +41,7 @@ struct AosArgs {
   int n_tiles;
   unsigned stage_bytes;  // bytes reserved per input stage (multiple of 128)
   unsigned out_bytes;    // bytes per output buffer (separate-output forms)
+  int native_warps;      // HYBRID: warps [0, native_warps) of every CTA compute natively
   unsigned* status;
   BMat<A> b;
 };
@@ -49,10 +50,11 @@ constexpr int kSmemHeader = 1024;  // mbarriers (<= 8 x 8 B) + b (<= 576 B), the
 
 // Stages b (72 reals) in shared memory and lets each thread's op take its direction j = tid % 4.
 template <class Op>
-__device__ __forceinline__ void load_b_op(const BMat<typename Op::BArg>& b, typename Op::BArg* bsh, Op& op) {
+__device__ __forceinline__ void load_b_op(const BMat<typename Op::BArg>& b, typename Op::BArg* bsh, Op& op,
+                                          int native_warps) {
   for (int i = threadIdx.x; i < 72; i += blockDim.x) bsh[i] = b.v[i];
   __syncthreads();
-  op.init(bsh + 18 * (threadIdx.x & 3));
+  op.init(bsh + 18 * (threadIdx.x & 3), native_warps);
 }
 
 // The AOS streaming kernel. Op::kNeIn complex elements per input link (9 full, 6 two-row),
@@ -80,7 +82,7 @@ __global__ void __launch_bounds__(256) su3_aos_kernel(const __grid_constant__ Ao
     fence_mbar_init();
   }
   Op op;
-  load_b_op(p.b, bsh, op);  // contains __syncthreads (also publishes the mbarrier init)
+  load_b_op(p.b, bsh, op, p.native_warps);  // contains __syncthreads (also publishes the mbarrier init)
 
   const uint64_t pol = policy_evict_first();
   const int my_tiles = p.n_tiles > (int)blockIdx.x ? (p.n_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
@@ -116,6 +118,7 @@ __global__ void __launch_bounds__(256) su3_aos_kernel(const __grid_constant__ Ao
     unsigned char* in = stage0 + (size_t)s * p.stage_bytes;
     unsigned char* out = kInPlace ? in : out0 + (size_t)(k % 3) * p.out_bytes;
     if (ok) {
+      op.begin_tile(k);
       for (int q = tid; q < 4 * nt; q += blockDim.x) {
         const int site = q >> 2, j = q & 3;
         const V* src = reinterpret_cast<const V*>(in + (size_t)site * p.a_stride + j * kLinkIn);
@@ -166,6 +169,7 @@ struct DirectArgs {
   const void* a;
   void* c;
   long long n_links;
+  int native_warps;       // HYBRID: warps [0, native_warps) of every CTA compute natively
   BMat<A> b;
 };
 
@@ -180,17 +184,20 @@ __global__ void __launch_bounds__(256) su3_direct_kernel(const __grid_constant__
   using V = typename Op::V;
   constexpr int NE_IN = Op::kNeIn, NE_OUT = Op::kNeOut;
   __shared__ typename Op::BArg bsh[72];
+  const long long q_end = p.n_links;
   Op op;
-  load_b_op(p.b, bsh, op);
+  load_b_op(p.b, bsh, op, p.native_warps);
   const V* a = reinterpret_cast<const V*>(p.a);
   V* c = reinterpret_cast<V*>(p.c);
   const long long T = (long long)gridDim.x * blockDim.x;  // a multiple of 4: j stays tid % 4
-  for (long long base = (long long)blockIdx.x * blockDim.x + threadIdx.x; base < p.n_links; base += LPT * T) {
+  int it = 0;
+  for (long long base = (long long)blockIdx.x * blockDim.x + threadIdx.x; base < q_end; base += LPT * T, ++it) {
+    op.begin_tile(it);
     V buf[LPT][NE_IN];
 #pragma unroll
     for (int u = 0; u < LPT; ++u) {
       const long long q = base + u * T;
-      if (q < p.n_links) {
+      if (q < q_end) {
 #pragma unroll
         for (int e = 0; e < NE_IN; ++e) buf[u][e] = ldg_stream(a + elem_index<LAYOUT, NE_IN>(q, e, p.n_links));
       }
@@ -198,7 +205,7 @@ __global__ void __launch_bounds__(256) su3_direct_kernel(const __grid_constant__
 #pragma unroll
     for (int u = 0; u < LPT; ++u) {
       const long long q = base + u * T;
-      if (q < p.n_links) {
+      if (q < q_end) {
         V res[NE_OUT];
         op.apply(buf[u], res);
 #pragma unroll
@@ -253,6 +260,11 @@ LaunchCfg default_cfg(const Form& f) {
     c.stages = 0;
     c.ctas_per_sm = 4;
   }
+  c.native_permille = f.arith == SU3_ARITH_HYBRID ? 125 : 0;
+  if (f.arith == SU3_ARITH_HYBRID) {
+    c.block = 256;  // 8 warps, one of them native
+    if (f.layout == SU3_LAYOUT_AOS) c.tile_sites = 64;  // 256 links: one per thread and tile
+  }
   return c;
 }
 
@@ -261,6 +273,13 @@ static BMat<A> make_b(const double* b) {
   BMat<A> m;
   for (int i = 0; i < 72; ++i) m.v[i] = (A)b[i];
   return m;
+}
+
+// HYBRID: warps per CTA on the FP64 pipe, the nearest to native_permille of the CTA's warps.
+static int native_warps(const Form& f, const LaunchCfg& cfg) {
+  if (f.arith != SU3_ARITH_HYBRID) return 0;
+  const int warps = cfg.block / 32;
+  return std::min(warps, (warps * cfg.native_permille + 500) / 1000);
 }
 
 static su3_status cuda_fail(const LaunchCtx& ctx, const char* what, cudaError_t e) {
@@ -286,6 +305,8 @@ static su3_status run_aos(const Form& f, const LaunchCfg& cfg, const void* a, co
   p.stage_bytes = (unsigned)(((long long)cfg.tile_sites * f.a_stride + 127) / 128 * 128);
   p.out_bytes =
       kInPlace ? 0u : (unsigned)(((long long)cfg.tile_sites * 4 * Op::kNeOut * sizeof(V) + 127) / 128 * 128);
+  p.native_warps = native_warps(f, cfg);
+  const int grid = (int)std::min<long long>(p.n_tiles, (long long)ctx.num_sms * cfg.ctas_per_sm);
   p.status = ctx.status;
   p.b = make_b<BA>(b);
   const size_t smem = kSmemHeader + (size_t)p.stages * p.stage_bytes + (kInPlace ? 0 : 3 * (size_t)p.out_bytes);
@@ -296,7 +317,6 @@ static su3_status run_aos(const Form& f, const LaunchCfg& cfg, const void* a, co
   auto kern = su3_aos_kernel<Op>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(ctx, "cudaFuncSetAttribute", e);
-  const int grid = (int)std::min<long long>(p.n_tiles, (long long)ctx.num_sms * cfg.ctas_per_sm);
   kern<<<grid, cfg.block, smem, ctx.stream>>>(p);
   e = cudaGetLastError();
   if (e != cudaSuccess) return cuda_fail(ctx, "su3_aos_kernel launch", e);
@@ -314,6 +334,7 @@ static su3_status run_direct(const Form& f, const LaunchCfg& cfg, const void* a,
   p.b = make_b<typename Op::BArg>(b);
   const int lpt = cfg.tile_sites;
   const long long per_cta = (long long)cfg.block * lpt;
+  p.native_warps = native_warps(f, cfg);
   const int grid = (int)std::max<long long>(1, std::min<long long>((p.n_links + per_cta - 1) / per_cta,
                                                                     (long long)ctx.num_sms * cfg.ctas_per_sm));
   switch (lpt) {
@@ -351,11 +372,14 @@ static su3_status run_repr(const Form& f, const LaunchCfg& cfg, const void* a, c
 
 su3_status launch_mult(const Form& f, const LaunchCfg& cfg, const void* a, const double* b, void* c,
                        const LaunchCtx& ctx) {
-  if (f.arith == SU3_ARITH_F32PAIR) {
+  if (f.arith == SU3_ARITH_F32PAIR || f.arith == SU3_ARITH_HYBRID) {
     if (f.dtype != SU3_F64) return SU3_ERR_UNSUPPORTED;
-    if (f.repr_in == SU3_REPR_FULL18) return run_layout<PairF64Op<9, 3>>(f, cfg, a, b, c, ctx);
-    if (f.repr_out == SU3_REPR_TWOROW12) return run_layout<PairF64Op<6, 2>>(f, cfg, a, b, c, ctx);
-    *ctx.err = "F32PAIR arithmetic does not rebuild row 2 (TWOROW12 -> FULL18)";
+    const bool hyb = f.arith == SU3_ARITH_HYBRID;
+    if (f.repr_in == SU3_REPR_FULL18)
+      return hyb ? run_layout<HybridF64Op<9, 3>>(f, cfg, a, b, c, ctx) : run_layout<PairF64Op<9, 3>>(f, cfg, a, b, c, ctx);
+    if (f.repr_out == SU3_REPR_TWOROW12)
+      return hyb ? run_layout<HybridF64Op<6, 2>>(f, cfg, a, b, c, ctx) : run_layout<PairF64Op<6, 2>>(f, cfg, a, b, c, ctx);
+    *ctx.err = "F32PAIR/HYBRID arithmetic does not rebuild row 2 (TWOROW12 -> FULL18)";
     return SU3_ERR_UNSUPPORTED;
   }
   switch (f.dtype) {

@@ -23,7 +23,7 @@ CACHE = os.path.join(os.path.dirname(os.path.abspath(__file__)), "tune_cache.jso
 DT = {"f64": B.F64, "f32": B.F32, "f16": B.F16, "bf16": B.BF16}
 RP = {"full": B.FULL18, "2row": B.TWOROW12}
 LY = {"aos": B.AOS, "aosoa32": B.AOSOA32, "soa": B.SOA}
-AR = {"native": B.NATIVE, "f32pair": B.F32PAIR}
+AR = {"native": B.NATIVE, "f32pair": B.F32PAIR, "hybrid": B.HYBRID}
 
 
 def form_name(desc):
@@ -36,7 +36,8 @@ def parse_form(name, n_sites=0):
     return B.Desc(DT[d], RP[r], LY[l], n_sites, 0, AR[a])
 
 
-ALL_FORMS = ["f64-full-aos", "f32-full-aos", "f16-full-aos", "bf16-full-aos", "f64-2row-aos", "f32-2row-aos",
+ALL_FORMS = ["f64-full-aos-hybrid", "f64-full-aosoa32-hybrid", "f64-2row-aos-hybrid", "f64-full-aos-f32pair",
+             "f64-full-aosoa32-f32pair", "f64-2row-aos-f32pair", "f64-full-aos", "f32-full-aos", "f16-full-aos", "bf16-full-aos", "f64-2row-aos", "f32-2row-aos",
              "f16-2row-aos", "f64-full-soa", "f32-full-soa", "f16-full-soa", "f64-full-aosoa32",
              "f32-full-aosoa32", "f16-full-aosoa32", "bf16-full-aosoa32"]
 
@@ -67,6 +68,15 @@ def apply_cached(h, key=None):
 
 
 def candidates(desc):
+    if desc.arith == B.HYBRID:
+        # one or two native warps per CTA; AOS tiles hold at least one link per thread
+        out = []
+        for c in candidates(B.Desc(desc.dtype, desc.repr, desc.layout, desc.n_sites, 0, B.F32PAIR)):
+            warps = c["block"] // 32
+            if desc.layout == B.AOS and c["tile_sites"] * 4 < c["block"]:
+                continue
+            out += [dict(c, native_permille=nw * 1000 // warps) for nw in (1, 2) if nw < warps]
+        return out
     if desc.layout == B.AOS:
         site = B.link_bytes(desc.dtype, desc.repr) * 4
         out = []

@@ -138,3 +138,26 @@ def test_f32pair_generic_and_constant_inputs(h):
     ac, bc = gen.paper_constant(4096)
     got = run_form(h, ac, bc, su3.F64, arith=su3.F32PAIR).reshape(-1, 72)
     assert np.max(np.abs(got[:, 0::2] - 1.0)) <= 1e-15 and np.max(np.abs(got[:, 1::2])) <= 1e-20
+
+
+@pytest.mark.parametrize("layout", LAYOUTS, ids=["aos", "aosoa32", "soa"])
+@pytest.mark.parametrize("rep", [su3.FULL18, su3.TWOROW12], ids=["full", "2row"])
+def test_hybrid_is_native_or_pair_per_site(layout, rep):
+    """HYBRID splits the lattice between FP64-pipe CTAs and FP32-pair CTAs: every site's result is
+    bit for bit the NATIVE or the F32PAIR result, about the configured share is native, and the
+    whole is within the FP64 tolerance of the oracle."""
+    hh = su3.Handle(0)
+    V = 9 * 8 ** 3 + 7
+    a, b = gen.lattice(11, V)
+    cfg = {"native_permille": 250}  # 2 of 8 warps: every 4th warp-tile runs natively
+    got = run_form(hh, a, b, su3.F64, rep, rep, layout, arith=su3.HYBRID, cfg=cfg).reshape(V, 72)
+    nat = run_form(hh, a, b, su3.F64, rep, rep, layout, arith=su3.NATIVE).reshape(V, 72)
+    pair = run_form(hh, a, b, su3.F64, rep, rep, layout, arith=su3.F32PAIR).reshape(V, 72)
+    is_nat = np.all(got == nat, axis=1)
+    is_pair = np.all(got == pair, axis=1)
+    assert np.all(is_nat | is_pair)
+    share = np.mean(is_nat & ~is_pair)
+    assert 0.18 < share < 0.32, share
+    mx, _ = oracle.error(got.reshape(-1), oracle.mult(a, b))
+    assert mx <= tol(su3.F64, rep)
+    hh.close()
