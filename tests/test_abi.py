@@ -57,9 +57,9 @@ def test_array_bytes_layouts():
 
 
 @pytest.mark.parametrize("bad", [
-    dict(dtype=7), dict(repr=2), dict(layout=3), dict(arith=2), dict(n_sites=-1),
+    dict(dtype=7), dict(repr=2), dict(layout=3), dict(arith=3), dict(n_sites=-1),
     dict(site_stride_bytes=8), dict(site_stride_bytes=584), dict(layout=su3.SOA, site_stride_bytes=576),
-    dict(dtype=su3.F32, arith=su3.F32PAIR),
+    dict(dtype=su3.F32, arith=su3.F32PAIR), dict(dtype=su3.F16, arith=su3.HYBRID),
 ])
 def test_descriptor_validation(bad):
     kw = dict(dtype=su3.F64, repr=su3.FULL18, layout=su3.AOS, n_sites=16, site_stride_bytes=0, arith=su3.NATIVE)
