@@ -461,9 +461,9 @@ su3_status su3_mult_host(su3_handle* h, const su3_desc* a_desc, const void* a_ho
     e = cudaEventCreateWithFlags(&h->ev_start, cudaEventDisableTiming);
     if (e != cudaSuccess) return cuda_err(h, "cudaEventCreate", e);
   }
-  // chunks of whole sites, a multiple of the kernel tile, ~256 MB of input each
+  // chunks of whole sites, a multiple of the kernel tile, ~64 MB of input each
   const int64_t a_site = f.a_stride, c_site = f.c_stride;
-  int64_t chunk = std::max<int64_t>(cfg.tile_sites, (256ll << 20) / a_site / cfg.tile_sites * cfg.tile_sites);
+  int64_t chunk = std::max<int64_t>(cfg.tile_sites, (64ll << 20) / a_site / cfg.tile_sites * cfg.tile_sites);
   chunk = std::min<int64_t>(chunk, f.n_sites);
   const size_t a_bytes = (size_t)(chunk * a_site), c_bytes = (size_t)(chunk * c_site);
   const size_t need = (a_bytes + 255) / 256 * 256 + c_bytes;

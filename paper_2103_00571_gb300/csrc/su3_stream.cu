@@ -300,11 +300,19 @@ static su3_status run_aos(const Form& f, const LaunchCfg& cfg, const void* a, co
   p.a_stride = f.a_stride;
   p.c_stride = f.c_stride;
   p.tile_sites = cfg.tile_sites;
+  if (!kInPlace) {
+    // the two-row -> full form shares its configuration with two-row -> two-row but also needs a
+    // 3-deep output ring: shrink the tile until both fit in shared memory
+    const long long out_site = 4LL * Op::kNeOut * (long long)sizeof(V);
+    while (p.tile_sites > 1 && kSmemHeader + (long long)cfg.stages * ((p.tile_sites * f.a_stride + 127) / 128 * 128) +
+                                       3 * ((p.tile_sites * out_site + 127) / 128 * 128) > 227 * 1024)
+      p.tile_sites = (p.tile_sites + 1) / 2;
+  }
   p.stages = cfg.stages;
-  p.n_tiles = (int)((f.n_sites + cfg.tile_sites - 1) / cfg.tile_sites);
-  p.stage_bytes = (unsigned)(((long long)cfg.tile_sites * f.a_stride + 127) / 128 * 128);
+  p.n_tiles = (int)((f.n_sites + p.tile_sites - 1) / p.tile_sites);
+  p.stage_bytes = (unsigned)(((long long)p.tile_sites * f.a_stride + 127) / 128 * 128);
   p.out_bytes =
-      kInPlace ? 0u : (unsigned)(((long long)cfg.tile_sites * 4 * Op::kNeOut * sizeof(V) + 127) / 128 * 128);
+      kInPlace ? 0u : (unsigned)(((long long)p.tile_sites * 4 * Op::kNeOut * sizeof(V) + 127) / 128 * 128);
   p.native_warps = native_warps(f, cfg);
   const int grid = (int)std::min<long long>(p.n_tiles, (long long)ctx.num_sms * cfg.ctas_per_sm);
   p.status = ctx.status;

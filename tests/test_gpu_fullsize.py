@@ -75,3 +75,16 @@ def test_L64_sampled(h, dtype):
     ref = oracle.mult_sites(gen.sites_at(gen.DEFAULT_SEED, 0, idx), b)
     mx, rms = oracle.error(got, ref)
     assert mx <= tol(dtype, su3.FULL18), (mx, rms)
+
+
+def test_every_bench_form_under_tuned_configs(h):
+    """Each form bench.py times, with the tuned launch configurations installed (the same handle
+    set-up bench.py uses), on a lattice spanning many tiles: within its tolerance of the oracle."""
+    import bench
+    V = 6 * 8 ** 3 + 11
+    a, b = gen.lattice(5, V)
+    ref = oracle.mult(a, b)
+    for name, dt, ri, ro, lay, *ar in bench.FORMS:
+        got = run_form(h, a, b, dt, ri, ro, lay, arith=ar[0] if ar else su3.NATIVE)
+        mx, _ = oracle.error(got, ref)
+        assert mx <= tol(dt, ri, ro), (name, mx)
