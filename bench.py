@@ -160,12 +160,16 @@ def cpu_baseline_leg(a_host, b, V_sample, min_seconds=10.0):
         n1 += 1
     el1 = time.perf_counter() - t1
     oracle.set_threads(cores)
+    # references of the adjacent operations on the same sample, for their error report
+    v = np.linspace(-0.5, 0.5, 24)
+    extra = {"an": oracle.mult_an(a, b), "na": oracle.mult_na(a, b), "v": v,
+             "mv": oracle.mat_vec(a, v), "mv_adj": oracle.mat_vec(a, v, adjoint=True)}
     summary = {"value": round(gbs, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
                "one_core_GBps": round(1152.0 * 65536 * n1 / el1 / 1e9, 3),
                "site_updates_per_s": round(V_sample * passes / el, 1),
                "sample": "%d sites (the first %d of the L=64 lattice) x %d passes, %.1f s, FP64, plain C "
                          "OpenMP loop over sites (the paper's VersionX form)" % (V_sample, V_sample, passes, el)}
-    return summary, ref
+    return summary, ref, extra
 
 
 def run_reference(args, world, rank):
@@ -332,11 +336,12 @@ def run_native(args, world, rank, local):
     if rank == 0 and not args.quick:
         # CPU baseline leg (oracle, as it stands, on the host cores; bounded sample)
         V_sample = min(V, 1 << 20)
-        cpu, ref = cpu_baseline_leg(a_host.numpy(), b, V_sample)
+        cpu, ref, extra = cpu_baseline_leg(a_host.numpy(), b, V_sample)
         line["cpu_baseline"] = cpu
         # speedup at error of every form on the same lattice
         line["forms"] = forms_leg(h, torch, su3, a_dev, b, V, stream, value, ref, V_sample)
         line["paper_site640"] = site640_leg(h, torch, su3, a_dev, b, V, stream, ref, V_sample)
+        line["adjacent_ops"] = adjacent_leg(h, torch, su3, a_dev, b, V, stream, extra, V_sample)
         fp64_err = sample_error(torch, c_dev, ref, V_sample)
         line["forms"]["f64-aos-" + args.arith] = {"GBps": round(value / world, 1), "site_updates_per_s": round(sups / world, 1),
                                     "speedup_vs_f64": 1.0, "max_err": fp64_err[0], "rms_err": fp64_err[1],
@@ -421,6 +426,51 @@ def site640_leg(h, torch, su3, a_dev, b, V, stream, ref, V_sample, reps=10):
                      "link_GBps_1152B": round(1152 * sups / 1e9, 1), "ms": round(per, 4), "max_err": err[0],
                      "tol": 1e-13, "ok": err[0] <= 1e-13}
     del abuf, cbuf
+    torch.cuda.empty_cache()
+    return res
+
+
+def adjacent_leg(h, torch, su3, a_dev, b, V, stream, extra, V_sample, reps=10):
+    """a b^dagger, a^dagger b, a v and a^dagger v over the same lattice (AOS), FP64 and FP32:
+    site-updates/s, algorithmic GB/s (link bytes read + output bytes written) and error."""
+    res = {}
+    vec = torch.empty(V * 24, dtype=torch.float64, device=a_dev.device)
+    for dt, dname in ((su3.F64, "f64"), (su3.F32, "f32")):
+        rb = 8 if dt == su3.F64 else 4
+        d = su3.Desc(dt, su3.FULL18, su3.AOS, V)
+        abuf = a_dev if dt == su3.F64 else torch.empty(su3.array_bytes(d), dtype=torch.uint8, device=a_dev.device)
+        if dt != su3.F64:
+            h.pack(a_dev, d, abuf, stream)
+        cbuf = torch.empty(su3.array_bytes(d), dtype=torch.uint8, device=a_dev.device)
+        wbuf = torch.empty(V * 24 * rb, dtype=torch.uint8, device=a_dev.device)
+        cases = [("a_bdag", lambda: h.mult_op(su3.OP_NA, d, abuf, b, d, cbuf, stream), 72 * rb, "na"),
+                 ("adag_b", lambda: h.mult_op(su3.OP_AN, d, abuf, b, d, cbuf, stream), 72 * rb, "an"),
+                 ("a_v", lambda: h.mat_vec(d, abuf, extra["v"], wbuf, False, stream), 24 * rb, "mv"),
+                 ("adag_v", lambda: h.mat_vec(d, abuf, extra["v"], wbuf, True, stream), 24 * rb, "mv_adj")]
+        for name, fn, out_bytes, key in cases:
+            for _ in range(3):
+                fn()
+            h.sync(stream)
+            _, per = time_launches(h, torch, fn, reps, stream)
+            h.sync(stream)
+            sups = V / (per * 1e-3)
+            if key in ("na", "an"):
+                c64 = torch.empty(V_sample * 72, dtype=torch.float64, device=a_dev.device)
+                h.unpack(su3.Desc(dt, su3.FULL18, su3.AOS, V_sample), cbuf, c64, stream)
+                h.sync(stream)
+                got = c64.cpu().numpy()
+            else:
+                raw = wbuf[: V_sample * 24 * rb].cpu().numpy()
+                got = raw.view(np.float64 if rb == 8 else np.float32).astype(np.float64)
+            diff = np.abs(got - extra[key])
+            tol = 1e-13 if dt == su3.F64 else 2e-6
+            res["%s-%s-aos" % (dname, name)] = {
+                "site_updates_per_s": round(sups, 1), "GBps": round((72 * rb + out_bytes) * sups / 1e9, 1),
+                "ms": round(per, 4), "max_err": float(diff.max()), "tol": tol, "ok": bool(diff.max() <= tol)}
+        del cbuf, wbuf
+        if dt != su3.F64:
+            del abuf
+    del vec
     torch.cuda.empty_cache()
     return res
 

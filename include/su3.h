@@ -136,6 +136,32 @@ su3_status su3_mult(su3_handle* h, const su3_desc* a_desc, const void* a_dev,
                     const double* b, const su3_desc* c_desc, void* c_dev, void* stream);
 
 /*
+ * The adjacent SU(3) products (the paper's introduction: matrix-matrix and matrix-vector SU(3)
+ * operations are the building blocks of lattice QCD codes such as MILC), with b fixed per link
+ * direction as in su3_mult:
+ *   SU3_OP_NN: c = a x b           (exactly su3_mult)
+ *   SU3_OP_NA: c = a x b^dagger    (b^dagger formed exactly on the host, then the su3_mult path;
+ *                                    every form su3_mult supports)
+ *   SU3_OP_AN: c = a^dagger x b    (its own kernel: AOS, FULL18 -> FULL18, NATIVE, any dtype)
+ * Same conventions as su3_mult (asynchronous, caller-owned 16-byte-aligned device buffers).
+ */
+typedef enum { SU3_OP_NN = 0, SU3_OP_NA = 1, SU3_OP_AN = 2 } su3_op;
+su3_status su3_mult_op(su3_handle* h, int32_t op, const su3_desc* a_desc, const void* a_dev,
+                       const double* b, const su3_desc* c_desc, void* c_dev, void* stream);
+
+/*
+ * Matrix x colour vector (MILC's mult_su3_mat_vec; with adjoint != 0 its adjoint form):
+ *   w[i][j][k] = sum_m a[i][j][k][m] v[j][m]        or   sum_m conj(a[i][j][m][k]) v[j][m].
+ * a: AOS FULL18 NATIVE array of any dtype (packed or strided sites); v: host FP64
+ * double v[4][3][2], one colour vector per link direction, copied at call time (rounded once to
+ * FP32 for F32/F16/BF16 storage); w_dev: packed array of n_sites x 4 colour vectors (3 complex
+ * each) in a's dtype, n_sites * 12 * 2 * sizeof(real) bytes, caller-owned, not overlapping a.
+ * Asynchronous on `stream`.
+ */
+su3_status su3_mat_vec(su3_handle* h, int32_t adjoint, const su3_desc* a_desc, const void* a_dev,
+                       const double* v, void* w_dev, void* stream);
+
+/*
  * The same operation with HOST buffers: a_host is copied to the device in chunks, multiplied
  * and copied back into c_host, with copies and kernels overlapped on the handle's streams.
  * Synchronous: returns when c_host is complete. Pinned host memory (cudaHostRegister or

@@ -53,6 +53,9 @@ def lib():
                 ("su3o_widen_half", [i64, vp, vp]),
                 ("su3o_widen_bf16", [i64, vp, vp]),
                 ("su3o_error", [i64, vp, vp, vp]),
+                ("su3o_mult_an", [i64, i64, vp, vp, vp]),
+                ("su3o_mult_na", [i64, i64, vp, vp, vp]),
+                ("su3o_mat_vec", [i64, i64, ctypes.c_int, vp, vp, vp]),
             ]:
                 f = getattr(L, name)
                 f.argtypes = args
@@ -89,6 +92,34 @@ def mult(a, b, site_stride=72):
     c = np.zeros_like(a)
     lib().su3o_mult(n, site_stride, _ptr(a), _ptr(b), _ptr(c))
     return c
+
+
+def mult_an(a, b, site_stride=72):
+    """c = a^dagger b per link (MILC's mult_su3_an): sum_m conj(a[m][k]) b[j][m][l]."""
+    a, b = _f64(a), _f64(b)
+    n = a.size // site_stride
+    c = np.zeros_like(a)
+    lib().su3o_mult_an(n, site_stride, _ptr(a), _ptr(b), _ptr(c))
+    return c
+
+
+def mult_na(a, b, site_stride=72):
+    """c = a b^dagger per link (MILC's mult_su3_na): sum_m a[k][m] conj(b[j][l][m])."""
+    a, b = _f64(a), _f64(b)
+    n = a.size // site_stride
+    c = np.zeros_like(a)
+    lib().su3o_mult_na(n, site_stride, _ptr(a), _ptr(b), _ptr(c))
+    return c
+
+
+def mat_vec(a, v, adjoint=False, site_stride=72):
+    """w[i][j] = a[i][j] v[j] (or a[i][j]^dagger v[j]); v: 24 doubles, w: n_sites*24 doubles."""
+    a, v = _f64(a), _f64(v)
+    assert v.size == 24, "v holds four colour vectors"
+    n = a.size // site_stride
+    w = np.zeros(n * 24, dtype=np.float64)
+    lib().su3o_mat_vec(n, site_stride, int(bool(adjoint)), _ptr(a), _ptr(v), _ptr(w))
+    return w
 
 
 def mult_sites(a_sel, b):

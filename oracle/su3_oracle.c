@@ -292,3 +292,97 @@ void su3o_set_threads(int n) {
   (void)n;
 #endif
 }
+
+/*
+ * Adjacent SU(3) operations of the same lattice shape (the paper's introduction names
+ * matrix-matrix and matrix-vector SU(3) operations as the building blocks of lattice QCD codes
+ * such as MILC; these are their plain definitions, one link at a time, b or v fixed per link
+ * direction j as in the SU3_Bench kernel):
+ *   su3o_mult_an: c[i][j][k][l] = sum_m conj(a[i][j][m][k]) * b[j][m][l]      (a^dagger b)
+ *   su3o_mult_na: c[i][j][k][l] = sum_m a[i][j][k][m] * conj(b[j][l][m])      (a b^dagger)
+ *   su3o_mat_vec: w[i][j][k]    = sum_m a[i][j][k][m] * v[j][m]               (a v)
+ *                 or, with adjoint != 0, sum_m conj(a[i][j][m][k]) * v[j][m]  (a^dagger v)
+ * v holds four colour vectors (4 x 3 complex = 24 doubles); w[n][4][3][2] is packed.
+ */
+void su3o_mult_an(int64_t n_sites, int64_t site_stride, const double* a, const double* b, double* c) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n_sites; ++i) {
+    for (int j = 0; j < 4; ++j) {
+      const double* A = a + i * site_stride + 18 * j;
+      const double* B = b + 18 * j;
+      double* C = c + i * site_stride + 18 * j;
+      for (int k = 0; k < 3; ++k) {
+        for (int l = 0; l < 3; ++l) {
+          double re = 0.0, im = 0.0;
+          for (int m = 0; m < 3; ++m) {
+            double ar = A[6 * m + 2 * k], ai = -A[6 * m + 2 * k + 1]; /* conj(a[m][k]) */
+            double br = B[6 * m + 2 * l], bi = B[6 * m + 2 * l + 1];
+            re = re + ar * br;
+            re = re - ai * bi;
+            im = im + ar * bi;
+            im = im + ai * br;
+          }
+          C[6 * k + 2 * l] = re;
+          C[6 * k + 2 * l + 1] = im;
+        }
+      }
+    }
+  }
+}
+
+void su3o_mult_na(int64_t n_sites, int64_t site_stride, const double* a, const double* b, double* c) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n_sites; ++i) {
+    for (int j = 0; j < 4; ++j) {
+      const double* A = a + i * site_stride + 18 * j;
+      const double* B = b + 18 * j;
+      double* C = c + i * site_stride + 18 * j;
+      for (int k = 0; k < 3; ++k) {
+        for (int l = 0; l < 3; ++l) {
+          double re = 0.0, im = 0.0;
+          for (int m = 0; m < 3; ++m) {
+            double ar = A[6 * k + 2 * m], ai = A[6 * k + 2 * m + 1];
+            double br = B[6 * l + 2 * m], bi = -B[6 * l + 2 * m + 1]; /* conj(b[l][m]) */
+            re = re + ar * br;
+            re = re - ai * bi;
+            im = im + ar * bi;
+            im = im + ai * br;
+          }
+          C[6 * k + 2 * l] = re;
+          C[6 * k + 2 * l + 1] = im;
+        }
+      }
+    }
+  }
+}
+
+void su3o_mat_vec(int64_t n_sites, int64_t site_stride, int adjoint, const double* a, const double* v, double* w) {
+#pragma omp parallel for schedule(static)
+  for (int64_t i = 0; i < n_sites; ++i) {
+    for (int j = 0; j < 4; ++j) {
+      const double* A = a + i * site_stride + 18 * j;
+      const double* X = v + 6 * j;
+      double* W = w + i * 24 + 6 * j;
+      for (int k = 0; k < 3; ++k) {
+        double re = 0.0, im = 0.0;
+        for (int m = 0; m < 3; ++m) {
+          double ar, ai;
+          if (adjoint) {
+            ar = A[6 * m + 2 * k];
+            ai = -A[6 * m + 2 * k + 1]; /* conj(a[m][k]) */
+          } else {
+            ar = A[6 * k + 2 * m];
+            ai = A[6 * k + 2 * m + 1];
+          }
+          double xr = X[2 * m], xi = X[2 * m + 1];
+          re = re + ar * xr;
+          re = re - ai * xi;
+          im = im + ar * xi;
+          im = im + ai * xr;
+        }
+        W[2 * k] = re;
+        W[2 * k + 1] = im;
+      }
+    }
+  }
+}

@@ -17,6 +17,7 @@ F64, F32, F16, BF16 = 0, 1, 2, 3
 FULL18, TWOROW12 = 0, 1
 AOS, AOSOA32, SOA = 0, 1, 2
 NATIVE, F32PAIR, HYBRID = 0, 1, 2
+OP_NN, OP_NA, OP_AN = 0, 1, 2
 
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_NOT_INITIALIZED, ERR_TIMEOUT, ERR_FAULT_INJECTED = range(7)
 
@@ -88,6 +89,10 @@ _SIGS = {
     "su3_get_batched_cfg": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(LaunchCfg)]),
     "su3_abi_version": (ctypes.c_int32, []),
     "su3_selftest_wait_timeout": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.c_void_p]),
+    "su3_mult_op": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(Desc), ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p]),
+    "su3_mat_vec": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(Desc), ctypes.c_void_p,
+                                   ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
 }
 
 
@@ -193,6 +198,19 @@ class Handle:
         self._check(lib().su3_mult(self._h, ctypes.byref(a_desc), _ptr(a), _ptr(b),
                                    ctypes.byref(c_desc) if c_desc is not None else None, _ptr(c),
                                    _stream_ptr(stream)), "su3_mult")
+
+    def mult_op(self, op, a_desc, a, b, c_desc, c, stream=None):
+        b = _b72(b)
+        self._check(lib().su3_mult_op(self._h, op, ctypes.byref(a_desc), _ptr(a), _ptr(b),
+                                      ctypes.byref(c_desc) if c_desc is not None else None, _ptr(c),
+                                      _stream_ptr(stream)), "su3_mult_op")
+
+    def mat_vec(self, a_desc, a, v, w, adjoint=False, stream=None):
+        v = np.ascontiguousarray(v, dtype=np.float64).reshape(-1)
+        if v.size != 24:
+            raise ValueError("v holds 4 colour vectors x 3 complex = 24 doubles")
+        self._check(lib().su3_mat_vec(self._h, int(bool(adjoint)), ctypes.byref(a_desc), _ptr(a), _ptr(v), _ptr(w),
+                                      _stream_ptr(stream)), "su3_mat_vec")
 
     def mult_host(self, a_desc, a_host, b, c_desc, c_host, stream=0):
         b = _b72(b)

@@ -354,6 +354,71 @@ su3_status su3_mult(su3_handle* h, const su3_desc* a_desc, const void* a_dev, co
   return launch_mult(f, cfg, a_dev, b, c_dev, ctx_of(h, (cudaStream_t)stream));
 }
 
+su3_status su3_mult_op(su3_handle* h, int32_t op, const su3_desc* a_desc, const void* a_dev, const double* b,
+                       const su3_desc* c_desc, void* c_dev, void* stream) {
+  if (!h) return SU3_ERR_NOT_INITIALIZED;
+  if (op == SU3_OP_NN) return su3_mult(h, a_desc, a_dev, b, c_desc, c_dev, stream);
+  if (!b) return fail(h, SU3_ERR_INVALID_ARG, "null b");
+  if (op == SU3_OP_NA) {
+    double bd[72];  // b^dagger: bd[j][k][l] = conj(b[j][l][k]) (exact)
+    for (int j = 0; j < 4; ++j)
+      for (int k = 0; k < 3; ++k)
+        for (int l = 0; l < 3; ++l) {
+          bd[18 * j + 6 * k + 2 * l] = b[18 * j + 6 * l + 2 * k];
+          bd[18 * j + 6 * k + 2 * l + 1] = -b[18 * j + 6 * l + 2 * k + 1];
+        }
+    return su3_mult(h, a_desc, a_dev, bd, c_desc, c_dev, stream);
+  }
+  if (op != SU3_OP_AN) return fail(h, SU3_ERR_INVALID_ARG, "op must be SU3_OP_NN, SU3_OP_NA or SU3_OP_AN");
+  if (!a_desc) return fail(h, SU3_ERR_INVALID_ARG, "null descriptor");
+  if (!c_desc) c_desc = a_desc;
+  Form f;
+  su3_status s = make_form(h, a_desc, c_desc, &f);
+  if (s != SU3_OK) return s;
+  if (f.layout != SU3_LAYOUT_AOS || f.repr_in != SU3_REPR_FULL18 || f.repr_out != SU3_REPR_FULL18 ||
+      f.arith != SU3_ARITH_NATIVE)
+    return fail(h, SU3_ERR_UNSUPPORTED, "a^dagger b takes AOS FULL18 arrays with NATIVE arithmetic");
+  if (f.n_sites == 0) return SU3_OK;
+  if (!a_dev || !c_dev || !aligned16(a_dev) || !aligned16(c_dev))
+    return fail(h, SU3_ERR_INVALID_ARG, "null or misaligned a or c");
+  const int64_t an = su3_array_bytes(a_desc), cn = su3_array_bytes(c_desc);
+  if (a_dev == c_dev) {
+    if (f.a_stride != f.c_stride) return fail(h, SU3_ERR_INVALID_ARG, "in-place operation needs identical strides");
+  } else if (ranges_overlap(a_dev, an, c_dev, cn)) {
+    return fail(h, SU3_ERR_INVALID_ARG, "a and c overlap without being the same array");
+  }
+  if (h->fault & kFaultLaunch) return fail(h, SU3_ERR_FAULT_INJECTED, "fault injected at launch");
+  LaunchCfg cfg = cfg_for(h, a_desc, f);
+  s = check_cfg(h, f, cfg);
+  if (s != SU3_OK) return s;
+  return launch_adjacent(0, f, cfg, a_dev, b, c_dev, ctx_of(h, (cudaStream_t)stream));
+}
+
+su3_status su3_mat_vec(su3_handle* h, int32_t adjoint, const su3_desc* a_desc, const void* a_dev, const double* v,
+                       void* w_dev, void* stream) {
+  if (!h) return SU3_ERR_NOT_INITIALIZED;
+  if (!a_desc || !v) return fail(h, SU3_ERR_INVALID_ARG, "null descriptor or v");
+  Form f;
+  su3_status s = make_form(h, a_desc, a_desc, &f);
+  if (s != SU3_OK) return s;
+  if (f.layout != SU3_LAYOUT_AOS || f.repr_in != SU3_REPR_FULL18 || f.arith != SU3_ARITH_NATIVE)
+    return fail(h, SU3_ERR_UNSUPPORTED, "matrix x vector takes AOS FULL18 arrays with NATIVE arithmetic");
+  if (f.n_sites == 0) return SU3_OK;
+  f.c_stride = 12 * 2 * real_bytes(f.dtype);  // 4 packed colour vectors per site
+  if (!a_dev || !w_dev || !aligned16(a_dev) || !aligned16(w_dev))
+    return fail(h, SU3_ERR_INVALID_ARG, "null or misaligned a or w");
+  if (ranges_overlap(a_dev, su3_array_bytes(a_desc), w_dev, f.n_sites * f.c_stride))
+    return fail(h, SU3_ERR_INVALID_ARG, "a and w overlap");
+  if (h->fault & kFaultLaunch) return fail(h, SU3_ERR_FAULT_INJECTED, "fault injected at launch");
+  LaunchCfg cfg = cfg_for(h, a_desc, f);
+  s = check_cfg(h, f, cfg);
+  if (s != SU3_OK) return s;
+  double vb[72] = {0};
+  for (int j = 0; j < 4; ++j)
+    for (int q = 0; q < 6; ++q) vb[18 * j + q] = v[6 * j + q];
+  return launch_adjacent(adjoint ? 2 : 1, f, cfg, a_dev, vb, w_dev, ctx_of(h, (cudaStream_t)stream));
+}
+
 su3_status su3_pack(su3_handle* h, const double* src, const su3_desc* dst, void* dst_dev, void* stream) {
   if (!h) return SU3_ERR_NOT_INITIALIZED;
   if (!dst || su3_check_desc(dst) != SU3_OK) return fail(h, SU3_ERR_INVALID_ARG, "invalid destination descriptor");

@@ -276,6 +276,91 @@ struct NativeOp {
   }
 };
 
+// ---- adjacent SU(3) operations ----------------------------------------------------------------
+// The lattice-QCD building blocks next to the benchmark's a x b: a^dagger x b (MILC's
+// mult_su3_an) and the matrix x colour-vector products a v and a^dagger v (mult_su3_mat_vec and
+// its adjoint), with b or v fixed per link direction exactly as in the SU3_Bench kernel.
+// (a x b^dagger needs no kernel of its own: b^dagger is formed exactly on the host.)
+
+template <int DT>
+struct AnOp {  // c[k][l] = sum_m conj(a[m][k]) b[m][l]
+  using S = Storage<DT>;
+  using A = typename S::acc;
+  using V = typename S::vec;
+  using BArg = A;
+  static constexpr int kNeIn = 9, kNeOut = 9;
+  A bre[9], bim[9];
+  __device__ __forceinline__ void begin_tile(int) {}
+  __device__ __forceinline__ void init(const BArg* bj, int) {
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      bre[e] = bj[2 * e];
+      bim[e] = bj[2 * e + 1];
+    }
+  }
+  __device__ __forceinline__ void apply(const V* src, V* dst) const {
+    Link<A> la;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) S::unpack(src[e], la.re[e], la.im[e]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+#pragma unroll
+      for (int l = 0; l < 3; ++l) {
+        // conj(a) = (ar, -ai): re += ar br + ai bi, im += ar bi - ai br
+        A re = la.re[k] * bre[l];
+        A im = la.re[k] * bim[l];
+        re = fma(la.im[k], bim[l], re);
+        im = fma(-la.im[k], bre[l], im);
+#pragma unroll
+        for (int m = 1; m < 3; ++m) {
+          re = fma(la.re[3 * m + k], bre[3 * m + l], re);
+          re = fma(la.im[3 * m + k], bim[3 * m + l], re);
+          im = fma(la.re[3 * m + k], bim[3 * m + l], im);
+          im = fma(-la.im[3 * m + k], bre[3 * m + l], im);
+        }
+        dst[3 * k + l] = S::pack(re, im);
+      }
+    }
+  }
+};
+
+template <int DT, bool ADJ>
+struct MatVecOp {  // w[k] = sum_m a[k][m] v[m]   (ADJ: sum_m conj(a[m][k]) v[m])
+  using S = Storage<DT>;
+  using A = typename S::acc;
+  using V = typename S::vec;
+  using BArg = A;
+  static constexpr int kNeIn = 9, kNeOut = 3;
+  A vre[3], vim[3];
+  __device__ __forceinline__ void begin_tile(int) {}
+  __device__ __forceinline__ void init(const BArg* vj, int) {
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      vre[m] = vj[2 * m];
+      vim[m] = vj[2 * m + 1];
+    }
+  }
+  __device__ __forceinline__ void apply(const V* src, V* dst) const {
+    Link<A> la;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) S::unpack(src[e], la.re[e], la.im[e]);
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      A re = 0, im = 0;
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const int e = ADJ ? 3 * m + k : 3 * k + m;
+        const A ai = ADJ ? -la.im[e] : la.im[e];
+        re = fma(la.re[e], vre[m], re);
+        re = fma(-ai, vim[m], re);
+        im = fma(la.re[e], vim[m], im);
+        im = fma(ai, vre[m], im);
+      }
+      dst[k] = S::pack(re, im);
+    }
+  }
+};
+
 // ---- FP64 storage with FP32-pair ("double-float") arithmetic ----------------------------------
 // GB300 issues FP64 FMAs at 1/64 of the FP32 rate, and even double<->float conversions run on the
 // FP64 pipe. This op keeps FP64 in memory but computes with unevaluated pairs of FP32 numbers:

@@ -52,6 +52,10 @@ LaunchCfg default_cfg(const Form& f);
 su3_status launch_mult(const Form& f, const LaunchCfg& cfg, const void* a, const double* b, void* c,
                        const LaunchCtx& ctx);
 
+// a^dagger b (which 0), a v (1), a^dagger v (2): AOS FULL18 NATIVE; v[j] at bv[18*j .. 18*j+5].
+su3_status launch_adjacent(int which, const Form& f, const LaunchCfg& cfg, const void* a, const double* bv, void* c,
+                           const LaunchCtx& ctx);
+
 // One CTA whose bounded mbarrier wait runs out after limit_ms (failure-path self test).
 su3_status launch_selftest_wait(int limit_ms, const LaunchCtx& ctx);
 

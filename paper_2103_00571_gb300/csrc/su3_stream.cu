@@ -399,4 +399,28 @@ su3_status launch_mult(const Form& f, const LaunchCfg& cfg, const void* a, const
   return SU3_ERR_UNSUPPORTED;
 }
 
+// a^dagger x b (which = 0), a v (1) and a^dagger v (2) over an AOS FULL18 array (NATIVE
+// arithmetic). For the matrix x vector forms `bv` holds v[j] at bv[18*j .. 18*j+5] and c is the
+// packed array of output colour vectors (4 per site).
+su3_status launch_adjacent(int which, const Form& f, const LaunchCfg& cfg, const void* a, const double* bv, void* c,
+                           const LaunchCtx& ctx) {
+  if (f.layout != SU3_LAYOUT_AOS || f.repr_in != SU3_REPR_FULL18 || f.arith != SU3_ARITH_NATIVE) {
+    *ctx.err = "adjacent operations take AOS FULL18 arrays with NATIVE arithmetic";
+    return SU3_ERR_UNSUPPORTED;
+  }
+#define SU3_ADJ_CASES(DT)                                                             \
+  case DT:                                                                            \
+    if (which == 0) return run_aos<AnOp<DT>>(f, cfg, a, bv, c, ctx);                  \
+    if (which == 1) return run_aos<MatVecOp<DT, false>>(f, cfg, a, bv, c, ctx);       \
+    return run_aos<MatVecOp<DT, true>>(f, cfg, a, bv, c, ctx);
+  switch (f.dtype) {
+    SU3_ADJ_CASES(kF64)
+    SU3_ADJ_CASES(kF32)
+    SU3_ADJ_CASES(kF16)
+    SU3_ADJ_CASES(kBF16)
+  }
+#undef SU3_ADJ_CASES
+  return SU3_ERR_UNSUPPORTED;
+}
+
 }  // namespace su3

@@ -298,3 +298,54 @@ def test_pins_catch_planted_mistakes(tmp_path, gen, name, old, new):
     L.su3o_mult(V, 72, a.ctypes.data, b.ctypes.data, c.ctypes.data)
     ref = np.einsum("sjkm,jml->sjkl", _cplx(a).reshape(V, 4, 3, 3), _cplx(b).reshape(4, 3, 3))
     assert np.max(np.abs(_cplx(c).reshape(V, 4, 3, 3) - ref)) > 1e-3, name
+
+
+def test_adjoint_products_match_einsum(oracle_lib, gen):
+    """a^dagger b and a b^dagger against numpy einsum with explicit conjugates/transposes."""
+    V = 16
+    a, b = gen.lattice(3, V)
+    A = _cplx(a).reshape(V, 4, 3, 3)
+    B = _cplx(b).reshape(4, 3, 3)
+    an = np.einsum("sjmk,jml->sjkl", A.conj(), B)
+    na = np.einsum("sjkm,jlm->sjkl", A, B.conj())
+    assert np.max(np.abs(_cplx(oracle_lib.mult_an(a, b)).reshape(V, 4, 3, 3) - an)) < 1e-15
+    assert np.max(np.abs(_cplx(oracle_lib.mult_na(a, b)).reshape(V, 4, 3, 3) - na)) < 1e-15
+
+
+def test_adjoint_products_of_a_matrix_with_itself_give_identity(oracle_lib, gen):
+    """For SU(3) U: U^dagger U = U U^dagger = I (every link of a set to its direction's b)."""
+    _, b = gen.lattice(8, 1)
+    a = np.tile(b, 5)  # 5 sites, link j = b[j]
+    eye = _real18(np.eye(3, dtype=complex)[None].repeat(20, 0)).reshape(-1)
+    assert np.max(np.abs(oracle_lib.mult_an(a, b) - eye)) < 1e-14
+    assert np.max(np.abs(oracle_lib.mult_na(a, b) - eye)) < 1e-14
+    # and the two differ for a generic a (catches a swapped conjugation)
+    a2, _ = gen.lattice(9, 5)
+    assert np.max(np.abs(oracle_lib.mult_an(a2, b) - oracle_lib.mult_na(a2, b))) > 0.1
+
+
+def test_mat_vec_matches_einsum_and_closed_forms(oracle_lib, gen):
+    V = 16
+    a, _ = gen.lattice(4, V)
+    rng = np.random.default_rng(6)
+    v = rng.standard_normal(24)
+    A = _cplx(a).reshape(V, 4, 3, 3)
+    X = (v[0::2] + 1j * v[1::2]).reshape(4, 3)
+    w = oracle_lib.mat_vec(a, v)
+    wa = oracle_lib.mat_vec(a, v, adjoint=True)
+    W = (w[0::2] + 1j * w[1::2]).reshape(V, 4, 3)
+    WA = (wa[0::2] + 1j * wa[1::2]).reshape(V, 4, 3)
+    assert np.max(np.abs(W - np.einsum("sjkm,jm->sjk", A, X))) < 1e-15
+    assert np.max(np.abs(WA - np.einsum("sjmk,jm->sjk", A.conj(), X))) < 1e-15
+    # closed forms: identity links return v; U^dagger applied to U's column k gives e_k
+    eye = _real18(np.eye(3, dtype=complex)[None].repeat(4, 0)).reshape(72)
+    assert np.array_equal(oracle_lib.mat_vec(eye, v), v)
+    U = A[0]  # 4 SU(3) matrices
+    col = np.stack([U[j][:, j % 3] for j in range(4)])
+    vv = np.empty(24)
+    vv[0::2] = col.real.reshape(-1)
+    vv[1::2] = col.imag.reshape(-1)
+    got = oracle_lib.mat_vec(a[:72], vv, adjoint=True)
+    G = (got[0::2] + 1j * got[1::2]).reshape(4, 3)
+    for j in range(4):
+        assert np.max(np.abs(G[j] - np.eye(3)[j % 3])) < 1e-15
