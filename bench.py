@@ -43,6 +43,8 @@ def parse():
     ap.add_argument("--quick", action="store_true", help="headline only: no forms/batched/e2e/cpu legs")
     ap.add_argument("--arith", default="native", choices=["native", "f32pair", "hybrid"],
                     help="arithmetic of the FP64 AoS step (native = the plain FP64 method)")
+    ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "f16", "bf16"],
+                    help="storage type of the timed step (other than f64: with --quick, for profiling)")
     return ap.parse_args()
 
 
@@ -273,8 +275,16 @@ def run_native(args, world, rank, local):
     a_dev = a_host.to(dev)
     c_dev = torch.empty_like(a_dev)
     arith = {"native": su3.NATIVE, "f32pair": su3.F32PAIR, "hybrid": su3.HYBRID}[args.arith]
-    d64 = su3.Desc(su3.F64, su3.FULL18, su3.AOS, V, 0, arith)
-    step = lambda: h.mult(d64, a_dev, b, d64, c_dev, stream)  # noqa: E731
+    dt = {"f64": su3.F64, "f32": su3.F32, "f16": su3.F16, "bf16": su3.BF16}[args.dtype]
+    if dt != su3.F64 and not args.quick:
+        raise SystemExit("--dtype other than f64 times the reduced form alone: use it with --quick")
+    d64 = su3.Desc(dt, su3.FULL18, su3.AOS, V, 0, arith if dt == su3.F64 else su3.NATIVE)
+    a_step, c_step = a_dev, c_dev
+    if dt != su3.F64:
+        a_step = torch.empty(su3.array_bytes(d64), dtype=torch.uint8, device=dev)
+        c_step = torch.empty_like(a_step)
+        h.pack(a_dev, d64, a_step, stream)
+    step = lambda: h.mult(d64, a_step, b, d64, c_step, stream)  # noqa: E731
 
     for _ in range(args.warmup):
         step()
@@ -289,7 +299,7 @@ def run_native(args, world, rank, local):
     h.sync(stream)
     launches = h.launch_count() - n_before
     total_ms = max_over_ranks(total_ms, world, dev)
-    bytes_per_step = 1152.0 * V
+    bytes_per_step = float(su3.site_update_bytes(dt)) * V
     value = world * bytes_per_step * args.steps / (total_ms * 1e-3) / 1e9
     sups = world * V * args.steps / (total_ms * 1e-3)
     clocks = clk.summary()
@@ -304,7 +314,11 @@ def run_native(args, world, rank, local):
         traffic = tr["bytes_per_site"] * V
     hbm_roof = {"achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(achieved_gbs / hbm_peak, 4), "peak_source": peak_src + " hbm_gbs"}
-    if args.arith == "native":
+    if dt != su3.F64:
+        tr = traffic_record().get("su3_aos_kernel<%s,full>" % args.dtype, {})
+        traffic = tr["bytes_per_site"] * V if tr and tr.get("source_digest") == source_digest() else None
+        roofline = dict(hbm_roof, bound="hbm", traffic=traffic, kernel="su3_aos_kernel<NativeOp<%s,9,3>>" % args.dtype)
+    elif args.arith == "native":
         roofline = {"bound": "alu", "achieved": round(achieved_tf, 4), "peak": round(fp64_peak, 4),
                     "unit": "TFLOP/s", "frac": round(achieved_tf / fp64_peak, 4), "traffic": traffic,
                     "kernel": "su3_aos_kernel<NativeOp<F64,9,3>>",
@@ -319,11 +333,14 @@ def run_native(args, world, rank, local):
     line = {"metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None,
-            "dtype": {"native": "f64", "f32pair": "f32x2 (FP64 storage)", "hybrid": "f64 + f32x2"}[args.arith],
+            "dtype": ({"native": "f64", "f32pair": "f32x2 (FP64 storage)", "hybrid": "f64 + f32x2"}[args.arith]
+                      if dt == su3.F64 else "%s storage, f32 math" % args.dtype),
             "data": "synthetic",
             "config": {"workload": "L=64 FP64 AoS SU3_Bench link multiply (c[i][j] = a[i][j] x b[j], "
                                    "%d sites, 576 B read + 576 B written per site)" % V,
-                       "lattice": "%d^4" % L, "form": "f64-full18-aos-" + args.arith, "seed": SEED,
+                       "lattice": "%d^4" % L,
+                       "form": ("f64-full18-aos-" + args.arith) if dt == su3.F64 else args.dtype + "-full18-aos",
+                       "seed": SEED,
                        "inputs": "random SU(3) (Gram-Schmidt on Gaussian rows), one lattice per GPU",
                        "l2": "inputs larger than L2 (%.1f GB touched per step vs 129 MB L2): no flush"
                              % (bytes_per_step / 1e9),
