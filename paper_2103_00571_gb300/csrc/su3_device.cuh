@@ -372,8 +372,12 @@ struct MatVecOp {  // w[k] = sum_m a[k][m] v[m]   (ADJ: sum_m conj(a[m][k]) v[m]
 //    Comput. 26 (2005)): products x_hi*y_hi are split exactly into p + e by an FMA (TwoProduct),
 //    the p's are summed with Knuth's TwoSum, and every error term (e, the TwoSum errors and the
 //    cross products x_hi*y_lo + x_lo*y_hi) is accumulated in a second FP32 number;
+//  * the real and imaginary parts of each complex output run as the two lanes of Blackwell's
+//    packed FP32x2 add/mul/fma, halving the FP32 instruction count;
 //  * the pair (s, L) becomes a double by building both halves' FP64 bit patterns with integer
-//    operations (exact for normal floats) and one FP64 add.
+//    operations (exact for normal floats) and one FP64 add. (Assembling it with integer
+//    operations only, to leave the FP64 pipe idle, measured slower: the extra integer work costs
+//    more issue slots than the FP64 add.)
 // Measured error against the FP64 oracle on random SU(3) data: max ~3e-14, RMS ~2e-15.
 
 struct FF {
@@ -400,31 +404,43 @@ __device__ __forceinline__ double f32_bits_to_f64(float f) {
   return __hiloint2double((int)hi, (int)(b << 29));
 }
 
-// sum_{t<6} x_t * y_t for pairs x = (xh, xl) (sign already folded in) and y = (yh, yl).
-// The error terms go to three independent accumulators (TwoSum errors, product errors, cross
+// Packed FP32x2 arithmetic (Blackwell's add/mul/fma.f32x2: two independent, individually
+// rounded FP32 operations per instruction). a - b is computed as fma(b, -1, a), which rounds
+// exactly like a subtraction.
+__device__ __forceinline__ float2 add2(float2 a, float2 b) { return __fadd2_rn(a, b); }
+__device__ __forceinline__ float2 mul2(float2 a, float2 b) { return __fmul2_rn(a, b); }
+__device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __ffma2_rn(a, b, c); }
+__device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
+
+// The real and imaginary parts of one complex output as two lanes of FP32x2 operations:
+// sum_{t<6} x_t * y_t with x = (xh, xl) broadcast to both lanes and y = (yh, yl) per lane. The
+// error terms go to three independent accumulators (TwoSum errors, product errors, cross
 // products) so that no dependency chain is longer than two operations per term.
-__device__ __forceinline__ double dot6_pair(const float (&xh)[6], const float (&xl)[6], const float (&yh)[6],
-                                            const float (&yl)[6]) {
-  float s = xh[0] * yh[0];
-  float Le = fmaf(xh[0], yh[0], -s);
-  float Lc = fmaf(xh[0], yl[0], xl[0] * yh[0]);
-  float Lt = 0.0f;
+__device__ __forceinline__ double2 dot6_pair2(const float (&xh)[6], const float (&xl)[6], const float2 (&yh)[6],
+                                              const float2 (&yl)[6]) {
+  const float2 zero = make_float2(0.f, 0.f);
+  float2 x0h = make_float2(xh[0], xh[0]), x0l = make_float2(xl[0], xl[0]);
+  float2 s = mul2(x0h, yh[0]);
+  float2 Le = fma2(x0h, yh[0], sub2(zero, s));
+  float2 Lc = fma2(x0h, yl[0], mul2(x0l, yh[0]));
+  float2 Lt = zero;
 #pragma unroll
   for (int t = 1; t < 6; ++t) {
-    const float p = xh[t] * yh[t];
-    const float s2 = s + p;
-    const float z = s2 - s;
-    const float t1 = s - (s2 - z);
-    const float t2 = p - z;
+    const float2 xth = make_float2(xh[t], xh[t]), xtl = make_float2(xl[t], xl[t]);
+    const float2 p = mul2(xth, yh[t]);
+    const float2 s2 = add2(s, p);
+    const float2 z = sub2(s2, s);
+    const float2 t1 = sub2(s, sub2(s2, z));
+    const float2 t2 = sub2(p, z);
     s = s2;
-    Lt = Lt + t1;
-    Lt = Lt + t2;
-    Le = Le + fmaf(xh[t], yh[t], -p);
-    Lc = fmaf(xh[t], yl[t], Lc);
-    Lc = fmaf(xl[t], yh[t], Lc);
+    Lt = add2(Lt, t1);
+    Lt = add2(Lt, t2);
+    Le = add2(Le, fma2(xth, yh[t], sub2(zero, p)));
+    Lc = fma2(xth, yl[t], Lc);
+    Lc = fma2(xtl, yh[t], Lc);
   }
-  const float L = (Lt + Le) + Lc;
-  return f32_bits_to_f64(s) + f32_bits_to_f64(L);
+  const float2 L = add2(add2(Lt, Le), Lc);
+  return make_double2(f32_bits_to_f64(s.x) + f32_bits_to_f64(L.x), f32_bits_to_f64(s.y) + f32_bits_to_f64(L.y));
 }
 
 template <int NE_IN, int ROWS_OUT>
@@ -432,64 +448,52 @@ struct PairF64Op {
   using V = double2;
   using BArg = double;
   static constexpr int kNeIn = NE_IN, kNeOut = 3 * ROWS_OUT;
-  // b[j] split once per thread: (hi, lo) of every real, [m][l] order
-  float brh[9], brl[9], bih[9], bil[9];
+  // b[j] split once per thread, as lane pairs for the two terms of each (m, l):
+  // (re, im) lanes of ar*(br, bi) and of ai*(-bi, br), high and low parts.
+  float2 ya[9], yb[9], yla[9], ylb[9];
   __device__ __forceinline__ void begin_tile(int) {}
   __device__ __forceinline__ void init(const double* bj, int /*native_warps*/) {
 #pragma unroll
     for (int e = 0; e < 9; ++e) {
       const double r = bj[2 * e], i = bj[2 * e + 1];
-      brh[e] = __double2float_rn(r);
-      brl[e] = __double2float_rn(r - (double)brh[e]);
-      bih[e] = __double2float_rn(i);
-      bil[e] = __double2float_rn(i - (double)bih[e]);
+      const float rh = __double2float_rn(r), ih = __double2float_rn(i);
+      const float rl = __double2float_rn(r - (double)rh), il = __double2float_rn(i - (double)ih);
+      ya[e] = make_float2(rh, ih);
+      yb[e] = make_float2(-ih, rh);
+      yla[e] = make_float2(rl, il);
+      ylb[e] = make_float2(-il, rl);
     }
   }
   __device__ __forceinline__ void apply(const V* src, V* dst) const {
-    float arh[9], arl[9], aih[9], ail[9];
-#pragma unroll
-    for (int e = 0; e < NE_IN; ++e) {
-      const double2 v = src[e];
-      const FF r = split_f64(v.x), i = split_f64(v.y);
-      arh[e] = r.h;
-      arl[e] = r.l;
-      aih[e] = i.h;
-      ail[e] = i.l;
-    }
     static_assert(NE_IN == 9 || ROWS_OUT == 2, "F32PAIR rebuilds no row 2");
 #pragma unroll
     for (int k = 0; k < ROWS_OUT; ++k) {
+      float xh[6], xl[6];  // terms 2m: a_re[k][m], 2m+1: a_im[k][m]
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const double2 v = src[3 * k + m];
+        const FF r = split_f64(v.x), i = split_f64(v.y);
+        xh[2 * m] = r.h;
+        xl[2 * m] = r.l;
+        xh[2 * m + 1] = i.h;
+        xl[2 * m + 1] = i.l;
+      }
 #pragma unroll
       for (int l = 0; l < 3; ++l) {
-        // re: sum_m ar*br - ai*bi ; im: sum_m ar*bi + ai*br
-        float xh[6], xl[6], yh[6], yl[6];
+        float2 yh[6], yl[6];
 #pragma unroll
         for (int m = 0; m < 3; ++m) {
-          xh[2 * m] = arh[3 * k + m];
-          xl[2 * m] = arl[3 * k + m];
-          yh[2 * m] = brh[3 * m + l];
-          yl[2 * m] = brl[3 * m + l];
-          xh[2 * m + 1] = -aih[3 * k + m];
-          xl[2 * m + 1] = -ail[3 * k + m];
-          yh[2 * m + 1] = bih[3 * m + l];
-          yl[2 * m + 1] = bil[3 * m + l];
+          yh[2 * m] = ya[3 * m + l];
+          yl[2 * m] = yla[3 * m + l];
+          yh[2 * m + 1] = yb[3 * m + l];
+          yl[2 * m + 1] = ylb[3 * m + l];
         }
-        const double re = dot6_pair(xh, xl, yh, yl);
-#pragma unroll
-        for (int m = 0; m < 3; ++m) {
-          xh[2 * m + 1] = aih[3 * k + m];
-          xl[2 * m + 1] = ail[3 * k + m];
-          yh[2 * m] = bih[3 * m + l];
-          yl[2 * m] = bil[3 * m + l];
-          yh[2 * m + 1] = brh[3 * m + l];
-          yl[2 * m + 1] = brl[3 * m + l];
-        }
-        const double im = dot6_pair(xh, xl, yh, yl);
-        dst[3 * k + l] = make_double2(re, im);
+        dst[3 * k + l] = dot6_pair2(xh, xl, yh, yl);
       }
     }
   }
 };
+
 
 // HYBRID: per tile, warp w uses the FP64 pipe (NATIVE) when (tile + w) % period == 0 and FP32
 // pairs otherwise, period = warps / native_warps. The native work rotates over all warps, so it
