@@ -540,8 +540,20 @@ def batched_leg(h, torch, su3, gen, reps=20):
         for d, abuf, bk, cbuf in per:
             h.mult(d, abuf, bk, d, cbuf, s)
 
+    # the same batch with its FP64 lattices in FP32-pair arithmetic
+    items_pair = []
+    for it in items:
+        d = it.desc
+        dp = su3.Desc(d.dtype, d.repr, d.layout, d.n_sites, d.site_stride_bytes,
+                      su3.F32PAIR if d.dtype == su3.F64 else su3.NATIVE)
+        items_pair.append(su3.BatchItem(dp, it.a_dev, it.c_dev, it.b))
+
+    def batched_pair():
+        h.mult_batched(items_pair, s, use_graph=True)
+
     res = {}
-    for name, fn in (("graph_persistent", batched), ("per_lattice_loop", loop)):
+    for name, fn in (("graph_persistent", batched), ("per_lattice_loop", loop),
+                     ("graph_persistent_f64_as_f32pair", batched_pair)):
         for _ in range(3):
             fn()
         h.sync(s)

@@ -72,8 +72,8 @@ typedef enum { SU3_LAYOUT_AOS = 0, SU3_LAYOUT_AOSOA32 = 1, SU3_LAYOUT_SOA = 2 } 
  * sum_m |a[k][m]||b[m][l]| per output (measured max 3e-14 against the FP64 oracle on SU(3)
  * data, whose entries are <= 1). Valid for finite inputs with |x| < 2^127; input magnitudes below
  * 2^-74 (including zeros) act as values below 2^-73. Supported reprs: FULL18 -> FULL18 and
- * TWOROW12 -> TWOROW12. Must be NATIVE for F32/F16/BF16 storage and for batched items
- * (HYBRID, below, likewise).
+ * TWOROW12 -> TWOROW12. Must be NATIVE for F32/F16/BF16 storage (HYBRID, below, likewise).
+ * Batched F64 items may use NATIVE or F32PAIR.
  */
 typedef enum { SU3_ARITH_NATIVE = 0, SU3_ARITH_F32PAIR = 1, SU3_ARITH_HYBRID = 2 } su3_arith;
 /*
@@ -106,7 +106,7 @@ typedef struct {
 
 /* One lattice of a batched call. a/c are device pointers; b as in su3_mult. */
 typedef struct {
-  su3_desc desc;     /* dtype F64 or F32, FULL18, AOS packed, arith NATIVE */
+  su3_desc desc;     /* dtype F64 or F32, FULL18, AOS packed; arith NATIVE, or F32PAIR for F64 */
   const void* a_dev;
   void* c_dev;
   double b[4][3][3][2];
@@ -176,7 +176,8 @@ su3_status su3_mult_host(su3_handle* h, const su3_desc* a_desc, const void* a_ho
  * kernel launch: the link tiles of all lattices form one global work list that the CTAs
  * stride over. With use_graph != 0 the launch (descriptor upload + kernel) is captured once into
  * a CUDA graph keyed by the item list and replayed with cudaGraphLaunch on later identical calls.
- * Supported items: dtype F64 or F32, FULL18, AOS packed, NATIVE. The item array is copied at
+ * Supported items: dtype F64 or F32, FULL18, AOS packed; NATIVE arithmetic, or F32PAIR for F64
+ * items (b is split into FP32 pairs on the host). The item array is copied at
  * call time into handle-owned device memory (the handle's workspace).
  */
 su3_status su3_mult_batched(su3_handle* h, int32_t n, const su3_batch_item* items, void* stream,
@@ -192,12 +193,12 @@ su3_status su3_mult_batched(su3_handle* h, int32_t n, const su3_batch_item* item
  * pool or fixed memory budget, and loops that must never stall, since cudaMalloc/cudaFree can
  * synchronise the whole device. Those callers cannot create a handle either (su3_init allocates),
  * so this entry point takes none and allocates nothing: the lattice descriptors go into a
- * statically allocated device area of 256 + SU3_STATIC_MAX_LATTICES * 608 bytes (about 152 KB),
+ * statically allocated device area of 256 + SU3_STATIC_MAX_LATTICES * 1192 bytes (about 298 KB),
  * which every GPU that loads libsu3 holds until the process exits.
  *  - Runs on the calling thread's current CUDA device. The first call on each device looks up the
  *    area's device address (set-up, once per device); make that first call before any stream
  *    capture.
- *  - Items follow su3_mult_batched's rules (F64 or F32, FULL18, packed AOS, NATIVE; a_dev/c_dev
+ *  - Items follow su3_mult_batched's rules (F64 or F32, FULL18, packed AOS, NATIVE or F64 F32PAIR; a_dev/c_dev
  *    caller-owned device buffers). More than SU3_STATIC_MAX_LATTICES non-empty items returns
  *    SU3_ERR_INVALID_ARG before anything is enqueued.
  *  - Synchronous: enqueues the descriptor upload and one kernel on `stream`, waits for `stream`,

@@ -591,8 +591,10 @@ static su3_status fill_batch(su3_handle* h, int32_t n, const su3_batch_item* ite
     const su3_desc& d = it.desc;
     if (su3_check_desc(&d) != SU3_OK) return fail(h, SU3_ERR_INVALID_ARG, "invalid descriptor in batch item " + std::to_string(i));
     if ((d.dtype != SU3_F64 && d.dtype != SU3_F32) || d.repr != SU3_REPR_FULL18 || d.layout != SU3_LAYOUT_AOS ||
-        d.arith != SU3_ARITH_NATIVE || (d.site_stride_bytes != 0 && d.site_stride_bytes != 4 * link_bytes(d.dtype, d.repr)))
-      return fail(h, SU3_ERR_UNSUPPORTED, "batched items must be F64 or F32, FULL18, packed AOS, NATIVE");
+        (d.arith != SU3_ARITH_NATIVE && !(d.arith == SU3_ARITH_F32PAIR && d.dtype == SU3_F64)) ||
+        (d.site_stride_bytes != 0 && d.site_stride_bytes != 4 * link_bytes(d.dtype, d.repr)))
+      return fail(h, SU3_ERR_UNSUPPORTED,
+                  "batched items must be F64 or F32, FULL18, packed AOS, NATIVE (or F32PAIR for F64)");
     if (d.n_sites == 0) continue;
     if (!it.a_dev || !it.c_dev || !aligned16(it.a_dev) || !aligned16(it.c_dev))
       return fail(h, SU3_ERR_INVALID_ARG, "null or misaligned pointer in batch item " + std::to_string(i));
@@ -605,7 +607,10 @@ static su3_status fill_batch(su3_handle* h, int32_t n, const su3_batch_item* ite
     o.n_sites = d.n_sites;
     o.dtype = d.dtype;
     o.first_tile = tiles;
+    o.arith = d.arith;
+    o.reserved = 0;
     memcpy(o.b, it.b, sizeof(o.b));
+    split_b_pairs(&it.b[0][0][0][0], o.bpair);
     const int64_t t = batch_tile_count(d.n_sites, h->bcfg.tile_sites);
     if ((int64_t)tiles + t > (1ll << 30)) return fail(h, SU3_ERR_INVALID_ARG, "batch too large");
     tiles += (int)t;

@@ -62,6 +62,16 @@ __device__ __forceinline__ void batch_tile_compute(unsigned char* in, int nt, co
   }
 }
 
+// FP64 lattice in FP32-pair arithmetic: b comes pre-split in the descriptor.
+__device__ __forceinline__ void batch_tile_compute_pair(unsigned char* in, int nt, const BatchDesc& d) {
+  PairF64Op<9, 3> op;
+  op.init_pre(d.bpair + 36 * (threadIdx.x & 3));
+  for (int q = threadIdx.x; q < 4 * nt; q += blockDim.x) {
+    double2* p = reinterpret_cast<double2*>(in + (size_t)q * 144);
+    op.apply(p, p);
+  }
+}
+
 __global__ void __launch_bounds__(256) su3_batched_kernel(const __grid_constant__ BatchArgs p) {
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
@@ -115,8 +125,12 @@ __global__ void __launch_bounds__(256) su3_batched_kernel(const __grid_constant_
     const BatchDesc& d = p.descs[ti.lattice];
     const int dtype = d.dtype;
     if (ok) {
-      if (dtype == SU3_F64) batch_tile_compute<kF64>(in, ti.nt, d);
-      else batch_tile_compute<kF32>(in, ti.nt, d);
+      if (dtype == SU3_F64) {
+        if (d.arith == SU3_ARITH_F32PAIR) batch_tile_compute_pair(in, ti.nt, d);
+        else batch_tile_compute<kF64>(in, ti.nt, d);
+      } else {
+        batch_tile_compute<kF32>(in, ti.nt, d);
+      }
     }
     fence_proxy_async_smem();
     if (__syncthreads_or(!ok)) {
@@ -214,7 +228,7 @@ su3_status launch_batched(const BatchDesc* descs_dev, int n, int total_tiles, co
 
 namespace su3 {
 
-static_assert(sizeof(BatchDesc) == 608, "the static area's documented size assumes 608-byte descriptors");
+static_assert(sizeof(BatchDesc) == 1192, "the static area's documented size assumes 1192-byte descriptors");
 constexpr size_t kStaticHeader = 256;
 constexpr size_t kStaticBytes = kStaticHeader + (size_t)SU3_STATIC_MAX_LATTICES * sizeof(BatchDesc);
 
@@ -258,7 +272,8 @@ extern "C" su3_status su3_mult_batched_static(int32_t n, const su3_batch_item* i
     const su3_desc& d = items[i].desc;
     if (su3_check_desc(&d) != SU3_OK) return SU3_ERR_INVALID_ARG;
     if ((d.dtype != SU3_F64 && d.dtype != SU3_F32) || d.repr != SU3_REPR_FULL18 || d.layout != SU3_LAYOUT_AOS ||
-        d.arith != SU3_ARITH_NATIVE || (d.site_stride_bytes != 0 && d.site_stride_bytes != 4 * link_bytes(d.dtype, d.repr)))
+        (d.arith != SU3_ARITH_NATIVE && !(d.arith == SU3_ARITH_F32PAIR && d.dtype == SU3_F64)) ||
+        (d.site_stride_bytes != 0 && d.site_stride_bytes != 4 * link_bytes(d.dtype, d.repr)))
       return SU3_ERR_UNSUPPORTED;
     if (d.n_sites == 0) continue;
     const void* a = items[i].a_dev;
@@ -295,7 +310,10 @@ extern "C" su3_status su3_mult_batched_static(int32_t n, const su3_batch_item* i
     o.n_sites = it.desc.n_sites;
     o.dtype = it.desc.dtype;
     o.first_tile = first_tile;
+    o.arith = it.desc.arith;
+    o.reserved = 0;
     memcpy(o.b, it.b, sizeof(o.b));
+    split_b_pairs(&it.b[0][0][0][0], o.bpair);
     first_tile += batch_tile_count(it.desc.n_sites, cfg.tile_sites);
     if (filled == kChunk || written + filled == m) {
       if (cudaMemcpyAsync(table + written, buf, sizeof(BatchDesc) * filled, cudaMemcpyHostToDevice, st) != cudaSuccess)

@@ -464,6 +464,18 @@ struct PairF64Op {
       ylb[e] = make_float2(-il, rl);
     }
   }
+  // The same constants from a host-side split: pre[4e..4e+3] = (re_hi, im_hi, re_lo, im_lo).
+  __device__ __forceinline__ void init_pre(const float* pre) {
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+      const float rh = __ldg(pre + 4 * e), ih = __ldg(pre + 4 * e + 1);
+      const float rl = __ldg(pre + 4 * e + 2), il = __ldg(pre + 4 * e + 3);
+      ya[e] = make_float2(rh, ih);
+      yb[e] = make_float2(-ih, rh);
+      yla[e] = make_float2(rl, il);
+      ylb[e] = make_float2(-il, rl);
+    }
+  }
   __device__ __forceinline__ void apply(const V* src, V* dst) const {
     static_assert(NE_IN == 9 || ROWS_OUT == 2, "F32PAIR rebuilds no row 2");
 #pragma unroll

@@ -70,8 +70,23 @@ struct BatchDesc {
   long long n_sites;
   int dtype;           // SU3_F64 or SU3_F32
   int first_tile;      // exclusive prefix sum of tile counts
+  int arith;           // SU3_ARITH_NATIVE, or SU3_ARITH_F32PAIR for F64 lattices
+  int reserved;
   double b[72];        // FP64 b (F32 lattices round it in the kernel)
+  float bpair[144];    // F32PAIR: b[j][e] split as (re_hi, im_hi, re_lo, im_lo), [j][e][4]
 };
+
+// Fills BatchDesc::bpair from the FP64 b (hi = b rounded to FP32, lo = the rest rounded to FP32).
+inline void split_b_pairs(const double* b, float* out) {
+  for (int q = 0; q < 36; ++q) {
+    const double r = b[2 * q], i = b[2 * q + 1];
+    const float rh = (float)r, ih = (float)i;
+    out[4 * q] = rh;
+    out[4 * q + 1] = ih;
+    out[4 * q + 2] = (float)(r - (double)rh);
+    out[4 * q + 3] = (float)(i - (double)ih);
+  }
+}
 
 struct BatchCfg {
   int block;

@@ -95,3 +95,28 @@ def test_batched_empty_and_rejects(h):
     z = su3.Desc(su3.F64, su3.FULL18, su3.AOS, 0)
     h.mult_batched([su3.BatchItem(z, 0, 0)], use_graph=False)
     h.sync()
+
+
+def test_batched_f32pair_items(h):
+    """FP64 lattices in FP32-pair arithmetic inside the batched launch: within the FP64 tolerance
+    of the oracle and bit for bit the single-lattice F32PAIR kernel's result."""
+    import torch
+    lat = make_batch(h, 16, seed=31, max_extent=10)
+    for L in lat:
+        if L["dt"] == su3.F64:
+            L["d"] = su3.Desc(su3.F64, su3.FULL18, su3.AOS, L["V"], 0, su3.F32PAIR)
+            L["item"].desc = L["d"]
+    for use_graph in (False, True):
+        h.mult_batched([L["item"] for L in lat], use_graph=use_graph)
+        h.sync()
+        for L in lat:
+            got = unpack(h, L)
+            tol = 1e-13 if L["dt"] == su3.F64 else 2e-6
+            assert oracle.error(got, oracle.mult(L["a"], L["b"]))[0] <= tol
+            if L["dt"] == su3.F64:
+                single = empty_bytes(su3.array_bytes(L["d"]))
+                h.mult(L["d"], L["abuf"], L["b"], L["d"], single)
+                o = torch.empty(L["V"] * 72, dtype=torch.float64, device="cuda")
+                h.unpack(L["d"], single, o)
+                h.sync()
+                assert np.array_equal(o.cpu().numpy(), got)
