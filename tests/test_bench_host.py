@@ -1,0 +1,50 @@
+"""Host-side logic of bench.py without a GPU: clock-record parsing, peaks, the source digest that
+invalidates stale ncu traffic records, the forms table, and the reference arm's JSON line."""
+import json
+import os
+import subprocess
+import sys
+
+import bench
+import paper_2103_00571_gb300 as su3
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_clock_summary_parses_nvidia_smi_rows():
+    c = bench.ClockSampler(0)
+    c.lines = ["0, 2070, 2070, 812.3, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+               "0, 1965, 2070, 1390.1, 0x0000000000000004, Not Active, Not Active, Not Active, Active",
+               "0, 2070, 2070, 900.0, 0x0000000000000000, Not Active, Not Active, Not Active, Not Active",
+               "garbage line"]
+    s = c.summary()
+    assert s["sm_mhz"] == 2070.0 and s["sm_max_mhz"] == 2070.0 and s["samples"] == 3
+    assert s["reasons"] == ["sw_power_cap"]
+    c.lines = []
+    assert c.summary()["samples"] == 0
+
+
+def test_peaks_and_digest():
+    hbm, smax, src = bench.peaks()
+    assert hbm > 1000 and smax > 1000 and src in ("measured", "fallback")
+    d1 = bench.source_digest()
+    assert len(d1) == 16 and d1 == bench.source_digest()
+
+
+def test_forms_table_is_valid():
+    names = set()
+    for name, dt, ri, ro, lay, *ar in bench.FORMS:
+        assert name not in names
+        names.add(name)
+        arith = ar[0] if ar else su3.NATIVE
+        assert su3.check_desc(su3.Desc(dt, ri, lay, 10, 0, arith)) == 0
+        assert su3.check_desc(su3.Desc(dt, ro, lay, 10, 0, arith)) == 0
+
+
+def test_reference_arm_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--L", "8",
+                          "--steps", "2", "--warmup", "1"], capture_output=True, text=True, check=True, cwd=ROOT)
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["unit"] == "GB/s" and line["value"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
+    assert line["metric"] == bench.METRIC and line["steps"] == 2 and line["higher_is_better"] is True
