@@ -48,8 +48,10 @@ def L48():
     return a, b, oracle.mult(a, b)
 
 
-@pytest.mark.parametrize("dtype", [su3.F64, su3.F16, su3.BF16, su3.F32])
-def test_L64_sampled(h, dtype):
+@pytest.mark.parametrize("dtype,arith", [(su3.F64, su3.NATIVE), (su3.F64, su3.F32PAIR), (su3.F16, su3.NATIVE),
+                                         (su3.BF16, su3.NATIVE), (su3.F32, su3.NATIVE)],
+                         ids=["f64", "f64-f32pair", "f16", "bf16", "f32"])
+def test_L64_sampled(h, dtype, arith):
     """L=64 (16.7M sites): the whole lattice runs on the GPU; 65,536 random sites are recomputed by
     the oracle from the same generator and compared element by element."""
     import torch
@@ -58,7 +60,7 @@ def test_L64_sampled(h, dtype):
     b = gen.bmat(gen.DEFAULT_SEED, 0, V)
     a_dev = torch.from_numpy(a).cuda()
     del a
-    d = su3.Desc(dtype, su3.FULL18, su3.AOS, V)
+    d = su3.Desc(dtype, su3.FULL18, su3.AOS, V, 0, arith)
     if dtype == su3.F64:
         abuf = a_dev
     else:
