@@ -309,7 +309,12 @@ static su3_status run_aos(const Form& f, const LaunchCfg& cfg, const void* a, co
       p.tile_sites = (p.tile_sites + 1) / 2;
   }
   p.stages = cfg.stages;
-  p.n_tiles = (int)((f.n_sites + p.tile_sites - 1) / p.tile_sites);
+  const long long n_tiles = (f.n_sites + p.tile_sites - 1) / p.tile_sites;
+  if (n_tiles > 0x7fffffffLL) {
+    *ctx.err = "too many tiles for one launch: use a larger tile_sites";
+    return SU3_ERR_INVALID_ARG;
+  }
+  p.n_tiles = (int)n_tiles;
   p.stage_bytes = (unsigned)(((long long)p.tile_sites * f.a_stride + 127) / 128 * 128);
   p.out_bytes =
       kInPlace ? 0u : (unsigned)(((long long)p.tile_sites * 4 * Op::kNeOut * sizeof(V) + 127) / 128 * 128);
