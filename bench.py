@@ -205,6 +205,9 @@ def run_reference(args, world, rank):
 
 # ---- the GPU legs -------------------------------------------------------------------------------
 
+LAST_LAUNCH_MS = []  # per-launch times of the most recent time_launches call
+
+
 def time_launches(h, torch, fn, n, stream):
     """Per-launch CUDA events on the launching stream; returns (total ms, mean ms per launch)."""
     evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(n)]
@@ -218,6 +221,7 @@ def time_launches(h, torch, fn, n, stream):
     last.record(stream)
     last.synchronize()
     per = [e0.elapsed_time(e1) for e0, e1 in evs]
+    LAST_LAUNCH_MS[:] = per
     return first.elapsed_time(last), sum(per) / len(per)
 
 
@@ -295,6 +299,7 @@ def run_native(args, world, rank, local):
     with ClockSampler(local) as clk:
         total_ms, per_launch_ms = time_launches(h, torch, step, args.steps, stream)
         torch.cuda.synchronize()
+    launch_ms = sorted(LAST_LAUNCH_MS)
     barrier(world)
     h.sync(stream)
     launches = h.launch_count() - n_before
@@ -348,7 +353,9 @@ def run_native(args, world, rank, local):
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "site_updates_per_s": round(sups, 1),
             "gflops": round(FLOP_PER_SITE * sups / 1e9, 2),
-            "roofline": roofline, "gpu_launches": launches, "clocks": clocks}
+            "roofline": roofline, "gpu_launches": launches, "clocks": clocks,
+            "launch_ms": {"mean": round(per_launch_ms, 4), "median": round(launch_ms[len(launch_ms) // 2], 4),
+                          "min": round(launch_ms[0], 4), "max": round(launch_ms[-1], 4)}}
 
     if rank == 0 and not args.quick:
         # CPU baseline leg (oracle, as it stands, on the host cores; bounded sample)

@@ -251,8 +251,9 @@ su3_status su3_check_desc(const su3_desc* d);
 su3_status su3_set_launch_cfg(su3_handle* h, const su3_desc* form, const su3_launch_cfg* cfg);
 su3_status su3_get_launch_cfg(su3_handle* h, const su3_desc* form, su3_launch_cfg* cfg);
 
-/* Launch configuration of su3_mult_batched (tile_sites = sites per work tile; the cached graph
- * is rebuilt on the next graph-mode call). 0 fields keep the current value. */
+/* Launch configuration of su3_mult_batched. A work tile is tile_sites * 576 bytes of input:
+ * tile_sites sites of an F64 lattice or 2 * tile_sites sites of an F32 lattice. The cached graph
+ * is rebuilt on the next graph-mode call. 0 fields keep the current value. */
 su3_status su3_set_batched_cfg(su3_handle* h, const su3_launch_cfg* cfg);
 su3_status su3_get_batched_cfg(su3_handle* h, su3_launch_cfg* cfg);
 

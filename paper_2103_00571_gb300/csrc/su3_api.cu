@@ -611,7 +611,7 @@ static su3_status fill_batch(su3_handle* h, int32_t n, const su3_batch_item* ite
     o.reserved = 0;
     memcpy(o.b, it.b, sizeof(o.b));
     split_b_pairs(&it.b[0][0][0][0], o.bpair);
-    const int64_t t = batch_tile_count(d.n_sites, h->bcfg.tile_sites);
+    const int64_t t = batch_tile_count(d.n_sites, d.dtype, h->bcfg.tile_sites);
     if ((int64_t)tiles + t > (1ll << 30)) return fail(h, SU3_ERR_INVALID_ARG, "batch too large");
     tiles += (int)t;
   }

@@ -2,12 +2,13 @@
 // storage, each with its own four b matrices) in ONE persistent launch.
 //
 // The tiles of all lattices form one global work list (lattice l owns tiles
-// first_tile[l] .. first_tile[l+1]-1). Each CTA strides over that list with the same shared-memory
+// first_tile[l] .. first_tile[l+1]-1). A tile is one shared-memory stage of bytes: tile_sites FP64
+// sites or 2 * tile_sites FP32 sites. Each CTA strides over that list with the same shared-memory
 // bulk-copy ring as the single-lattice AOS kernel; the thread issuing a tile's copy looks its
-// lattice up by binary search over first_tile and leaves (lattice, first site, sites, dtype) next
-// to the stage, where the computing threads read it after the stage's mbarrier completes. Each
-// tile's link products use that lattice's b (read through the L1 cache; FP32 lattices round it to
-// FP32 once per load).
+// lattice up (a galloping search forward from the previous tile's lattice, since a CTA's tiles
+// come in increasing order) and leaves (lattice, first site, sites) next to the stage, where the
+// computing threads read it after the stage's mbarrier completes. Each tile's link products use
+// that lattice's b (read through the L1 cache; FP32 lattices round it to FP32 once per load).
 #include <cuda_runtime.h>
 
 #include <string.h>
@@ -89,17 +90,26 @@ __global__ void __launch_bounds__(256) su3_batched_kernel(const __grid_constant_
       p.total_tiles > (int)blockIdx.x ? (p.total_tiles - 1 - (int)blockIdx.x) / (int)gridDim.x + 1 : 0;
 
   // thread 0 only: find the tile's lattice, record it beside the stage, start the copy
+  int cur = 0;  // lattice of the previous tile (thread 0's state): tiles come in increasing order
   auto issue_load = [&](int k) {
     const int t = (int)blockIdx.x + k * (int)gridDim.x;
-    int lo = 0, hi = p.n - 1;  // last lattice with first_tile <= t
+    // last lattice with first_tile <= t: gallop forward from cur, then bisect
+    int lo = cur, step = 1;
+    while (lo + step < p.n && p.descs[lo + step].first_tile <= t) {
+      lo += step;
+      step <<= 1;
+    }
+    int hi = min(lo + step, p.n) - 1;
     while (lo < hi) {
       const int mid = (lo + hi + 1) >> 1;
       if (p.descs[mid].first_tile <= t) lo = mid; else hi = mid - 1;
     }
+    cur = lo;
     const BatchDesc& d = p.descs[lo];
-    const long long first = (long long)(t - d.first_tile) * p.tile_sites;
+    const int ts = batch_tile_sites(d.dtype, p.tile_sites);
+    const long long first = (long long)(t - d.first_tile) * ts;
     long long rest = d.n_sites - first;
-    const int nt = (int)(rest < p.tile_sites ? rest : p.tile_sites);
+    const int nt = (int)(rest < ts ? rest : ts);
     const int s = k % S_;
     info[s].lattice = lo;
     info[s].nt = nt > 0 ? nt : 0;
@@ -157,15 +167,20 @@ __global__ void __launch_bounds__(256) su3_batched_kernel(const __grid_constant_
 }
 
 BatchCfg default_batch_cfg() {
+  // measured best on GB300 for the 96-lattice FP64/FP32 mix (and for its FP32-pair variant):
+  // four 64-thread CTAs per SM, 32-site (18 KB) stages, three deep
   BatchCfg c;
-  c.block = 128;
+  c.block = 64;
   c.tile_sites = 32;
-  c.stages = 4;
-  c.ctas_per_sm = 2;
+  c.stages = 3;
+  c.ctas_per_sm = 4;
   return c;
 }
 
-int batch_tile_count(long long n_sites, int tile_sites) { return (int)((n_sites + tile_sites - 1) / tile_sites); }
+int batch_tile_count(long long n_sites, int dtype, int tile_sites) {
+  const int ts = batch_tile_sites(dtype, tile_sites);
+  return (int)((n_sites + ts - 1) / ts);
+}
 
 static size_t batch_smem(const BatchCfg& cfg) {
   return kBatchHeader + (size_t)cfg.stages * (((size_t)cfg.tile_sites * 576 + 127) / 128 * 128);
@@ -282,7 +297,7 @@ extern "C" su3_status su3_mult_batched_static(int32_t n, const su3_batch_item* i
     const uintptr_t nb = (uintptr_t)(d.n_sites * 4 * link_bytes(d.dtype, d.repr));
     if (a != c && (uintptr_t)a < (uintptr_t)c + nb && (uintptr_t)c < (uintptr_t)a + nb) return SU3_ERR_INVALID_ARG;
     ++m;
-    tiles += batch_tile_count(d.n_sites, cfg.tile_sites);
+    tiles += batch_tile_count(d.n_sites, d.dtype, cfg.tile_sites);
   }
   if (m > SU3_STATIC_MAX_LATTICES || tiles > (1ll << 30)) return SU3_ERR_INVALID_ARG;
   if (m == 0) return SU3_OK;
@@ -314,7 +329,7 @@ extern "C" su3_status su3_mult_batched_static(int32_t n, const su3_batch_item* i
     o.reserved = 0;
     memcpy(o.b, it.b, sizeof(o.b));
     split_b_pairs(&it.b[0][0][0][0], o.bpair);
-    first_tile += batch_tile_count(it.desc.n_sites, cfg.tile_sites);
+    first_tile += batch_tile_count(it.desc.n_sites, it.desc.dtype, cfg.tile_sites);
     if (filled == kChunk || written + filled == m) {
       if (cudaMemcpyAsync(table + written, buf, sizeof(BatchDesc) * filled, cudaMemcpyHostToDevice, st) != cudaSuccess)
         return SU3_ERR_CUDA;

@@ -96,7 +96,9 @@ struct BatchCfg {
 };
 
 BatchCfg default_batch_cfg();
-int batch_tile_count(long long n_sites, int tile_sites);
+// Tiles are sized in bytes: tile_sites FP64 sites, or 2 * tile_sites FP32 sites (576 B vs 288 B each).
+__host__ __device__ inline int batch_tile_sites(int dtype, int tile_sites) { return dtype == SU3_F64 ? tile_sites : 2 * tile_sites; }
+int batch_tile_count(long long n_sites, int dtype, int tile_sites);
 
 // Validates a batched configuration and sets the kernel's shared-memory attribute.
 su3_status prepare_batched(const BatchCfg& cfg, std::string* err);

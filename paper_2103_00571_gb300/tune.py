@@ -158,8 +158,8 @@ def tune_batched(h, log=print):
         items.append(B.BatchItem(d, abuf.data_ptr(), cbuf.data_ptr(),
                                  (ctypes.c_double * 72)(*gen.bmat(gen.DEFAULT_SEED, k, V))))
     best = None
-    for block, ts, stages, cps in itertools.product((128, 256), (16, 32, 64), (3, 4, 6), (1, 2, 3)):
-        if 1024 + stages * ((ts * 576 + 127) // 128 * 128) > 227 * 1024 // cps:
+    for block, ts, stages, cps in itertools.product((64, 128, 256), (16, 32, 64), (2, 3, 4), (1, 2, 3, 4, 6)):
+        if 1024 + stages * ((ts * 576 + 127) // 128 * 128) > 227 * 1024 // cps or block * cps > 1024:
             continue
         cfg = dict(block=block, tile_sites=ts, stages=stages, ctas_per_sm=cps)
         h.set_batched_cfg(**cfg)

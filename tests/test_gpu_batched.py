@@ -120,3 +120,37 @@ def test_batched_f32pair_items(h):
                 h.unpack(L["d"], single, o)
                 h.sync()
                 assert np.array_equal(o.cpu().numpy(), got)
+
+
+def test_batched_many_small_lattices(h):
+    """Hundreds of lattices of 1..97 sites (FP64, FP32 and FP64 in FP32 pairs) under small tiles:
+    many lattices fall between two tiles of one CTA, FP32 lattices take twice the sites per tile,
+    and most tiles are ragged. Each lattice against its own oracle, with and without a graph."""
+    import torch
+    saved = h.get_batched_cfg()
+    try:
+        h.set_batched_cfg(block=64, tile_sites=8, stages=3, ctas_per_sm=2)
+        lat = []
+        for k in range(300):
+            V = 1 + (k * 37) % 97
+            a, b = gen.lattice(41, V, lattice_id=k)
+            kind = k % 3
+            dt = su3.F32 if kind == 1 else su3.F64
+            d = su3.Desc(dt, su3.FULL18, su3.AOS, V, 0, su3.F32PAIR if kind == 2 else su3.NATIVE)
+            abuf = empty_bytes(su3.array_bytes(d))
+            h.pack(to_dev(a), d, abuf)
+            cbuf = empty_bytes(su3.array_bytes(d))
+            item = su3.BatchItem(d, abuf.data_ptr(), cbuf.data_ptr(), (ctypes.c_double * 72)(*b))
+            lat.append(dict(a=a, b=b, d=d, abuf=abuf, cbuf=cbuf, item=item, V=V, dt=dt))
+        h.sync()
+        for use_graph in (False, True):
+            for L in lat:
+                L["cbuf"].fill_(0)
+            h.mult_batched([L["item"] for L in lat], use_graph=use_graph)
+            h.sync()
+            for L in lat:
+                tol = 1e-13 if L["dt"] == su3.F64 else 2e-6
+                assert oracle.error(unpack(h, L), oracle.mult(L["a"], L["b"]))[0] <= tol
+    finally:
+        h.set_batched_cfg(**saved)
+        torch.cuda.synchronize()
