@@ -233,11 +233,16 @@ def traffic_record():
         return json.load(f)
 
 
+# the sources that define the single-lattice AoS kernels (the ones the traffic records describe)
+AOS_KERNEL_SOURCES = ("su3_device.cuh", "su3_internal.h", "su3_stream.cu")
+
+
 def source_digest():
+    """Digest of the AoS kernels' sources: a traffic record taken under another digest is stale."""
     import hashlib
     d = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2103_00571_gb300", "csrc")
-    for n in sorted(os.listdir(csrc)):
+    for n in AOS_KERNEL_SOURCES:
         with open(os.path.join(csrc, n), "rb") as f:
             d.update(n.encode() + f.read())
     return d.hexdigest()[:16]
