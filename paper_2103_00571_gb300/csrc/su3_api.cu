@@ -43,6 +43,7 @@ constexpr int kHostBuffers = 3;
 struct su3_handle {
   int device = 0;
   int num_sms = 0;
+  int smem_per_sm = 0, smem_reserved = 0;
   unsigned* status_dev = nullptr;
   int64_t launches = 0;
   std::string err;
@@ -88,6 +89,8 @@ LaunchCtx ctx_of(su3_handle* h, cudaStream_t st) {
   c.stream = st;
   c.status = h->status_dev;
   c.num_sms = h->num_sms;
+  c.smem_per_sm = h->smem_per_sm;
+  c.smem_reserved = h->smem_reserved;
   c.launches = &h->launches;
   c.err = &h->err;
   return c;
@@ -223,6 +226,10 @@ su3_status su3_init(int device, su3_handle** out) {
   }
   cudaError_t e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&h->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
+  if (e == cudaSuccess)
+    e = cudaDeviceGetAttribute(&h->smem_reserved, cudaDevAttrReservedSharedMemoryPerBlock, device);
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->status_dev, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(h->status_dev, 0, sizeof(unsigned));
   if (e != cudaSuccess) {

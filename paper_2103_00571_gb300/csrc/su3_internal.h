@@ -37,6 +37,8 @@ struct LaunchCtx {
   cudaStream_t stream;
   unsigned* status;  // device status word
   int num_sms;
+  int smem_per_sm = 0;    // shared memory per SM in bytes (0: unknown, no fitting)
+  int smem_reserved = 0;  // shared memory the system reserves per CTA
   int64_t* launches;  // incremented per kernel launch
   std::string* err;
 };

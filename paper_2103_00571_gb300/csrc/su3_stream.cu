@@ -308,6 +308,23 @@ static su3_status run_aos(const Form& f, const LaunchCfg& cfg, const void* a, co
                                        3 * ((p.tile_sites * out_site + 127) / 128 * 128) > 227 * 1024)
       p.tile_sites = (p.tile_sites + 1) / 2;
   }
+  // keep ctas_per_sm CTAs resident: a tile shape tuned for the packed stride needs more shared
+  // memory at a padded stride (640 B sites), so shrink the tile (to a multiple of 8 sites) until
+  // that many CTAs fit in one SM's shared memory instead of silently running fewer
+  if (ctx.smem_per_sm > 0) {
+    const long long out_site = 4LL * Op::kNeOut * (long long)sizeof(V);
+    auto smem_of = [&](long long ts) {
+      return kSmemHeader + (long long)cfg.stages * ((ts * f.a_stride + 127) / 128 * 128) +
+             (kInPlace ? 0 : 3 * ((ts * out_site + 127) / 128 * 128));
+    };
+    const long long per_cta = ctx.smem_per_sm / cfg.ctas_per_sm - ctx.smem_reserved;
+    if (smem_of(p.tile_sites) > per_cta) {
+      long long ts = p.tile_sites;
+      while (ts > 1 && smem_of(ts) > per_cta) --ts;
+      if (ts >= 8) ts &= ~7LL;
+      p.tile_sites = (int)ts;
+    }
+  }
   p.stages = cfg.stages;
   const long long n_tiles = (f.n_sites + p.tile_sites - 1) / p.tile_sites;
   if (n_tiles > 0x7fffffffLL) {

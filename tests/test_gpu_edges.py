@@ -55,24 +55,33 @@ def test_in_place(h):
         assert oracle.error(out.cpu().numpy(), ref)[0] <= (1e-13 if dt == su3.F64 else 2e-6)
 
 
-def test_stride_640_keeps_pads_and_canaries(h):
+@pytest.mark.parametrize("arith", [su3.NATIVE, su3.F32PAIR])
+@pytest.mark.parametrize("cfg", [None, dict(block=256, tile_sites=64, stages=3, ctas_per_sm=2)])
+def test_stride_640_keeps_pads_and_canaries(h, arith, cfg):
     """The paper's padded 640-byte FP64 site: the kernel never writes bytes 576..639 of a site,
-    nor anything outside c (4 KiB canaries on both sides)."""
+    nor anything outside c (4 KiB canaries on both sides). The second shape is the packed-stride
+    tuned one, which at 640 B needs a smaller tile to keep two CTAs per SM."""
     import torch
-    V = 2051
+    V = 20051
     a, b = gen.lattice(4, V)
     stride = 640
     a640 = np.full((V, 80), -3.25)
     a640[:, :72] = a.reshape(V, 72)
     canary = 4096
-    d = su3.Desc(su3.F64, su3.FULL18, su3.AOS, V, stride)
-    cbig = torch.full((canary * 2 + V * stride,), 0xA5, dtype=torch.uint8, device="cuda")
-    cview_ptr = cbig.data_ptr() + canary
-    # pads of c pre-filled with a pattern
-    cbig[canary:canary + V * stride].view(torch.float64).view(V, 80)[:, 72:] = 9.5
-    a_dev = to_dev(a640.reshape(-1))
-    h.mult(d, a_dev, b, d, cview_ptr)
-    h.sync()
+    d = su3.Desc(su3.F64, su3.FULL18, su3.AOS, V, stride, arith)
+    saved = h.get_launch_cfg(d)
+    if cfg:
+        h.set_launch_cfg(d, **cfg)
+    try:
+        cbig = torch.full((canary * 2 + V * stride,), 0xA5, dtype=torch.uint8, device="cuda")
+        cview_ptr = cbig.data_ptr() + canary
+        # pads of c pre-filled with a pattern
+        cbig[canary:canary + V * stride].view(torch.float64).view(V, 80)[:, 72:] = 9.5
+        a_dev = to_dev(a640.reshape(-1))
+        h.mult(d, a_dev, b, d, cview_ptr)
+        h.sync()
+    finally:
+        h.set_launch_cfg(d, **saved)
     host = cbig.cpu().numpy()
     assert np.all(host[:canary] == 0xA5) and np.all(host[-canary:] == 0xA5)
     c = host[canary:canary + V * stride].view(np.float64).reshape(V, 80)
