@@ -136,8 +136,8 @@ su3_status su3_mult(su3_handle* h, const su3_desc* a_desc, const void* a_dev,
                     const double* b, const su3_desc* c_desc, void* c_dev, void* stream);
 
 /*
- * The adjacent SU(3) products (the paper's introduction: matrix-matrix and matrix-vector SU(3)
- * operations are the building blocks of lattice QCD codes such as MILC), with b fixed per link
+ * The adjacent SU(3) products (the paper's introduction places SU(3) products with matrices and
+ * with colour vectors at the core of lattice-QCD codes such as MILC), with b fixed per link
  * direction as in su3_mult:
  *   SU3_OP_NN: c = a x b           (exactly su3_mult)
  *   SU3_OP_NA: c = a x b^dagger    (b^dagger formed exactly on the host, then the su3_mult path;

@@ -294,10 +294,10 @@ void su3o_set_threads(int n) {
 }
 
 /*
- * Adjacent SU(3) operations of the same lattice shape (the paper's introduction names
- * matrix-matrix and matrix-vector SU(3) operations as the building blocks of lattice QCD codes
- * such as MILC; these are their plain definitions, one link at a time, b or v fixed per link
- * direction j as in the SU3_Bench kernel):
+ * Adjacent SU(3) operations of the same lattice shape (the paper's introduction places SU(3)
+ * products with matrices and with colour vectors at the core of lattice-QCD codes such as MILC;
+ * these are their plain definitions, one link at a time, b or v fixed per link direction j as in
+ * the SU3_Bench kernel):
  *   su3o_mult_an: c[i][j][k][l] = sum_m conj(a[i][j][m][k]) * b[j][m][l]      (a^dagger b)
  *   su3o_mult_na: c[i][j][k][l] = sum_m a[i][j][k][m] * conj(b[j][l][m])      (a b^dagger)
  *   su3o_mat_vec: w[i][j][k]    = sum_m a[i][j][k][m] * v[j][m]               (a v)
