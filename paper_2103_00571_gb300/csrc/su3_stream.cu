@@ -263,7 +263,10 @@ LaunchCfg default_cfg(const Form& f) {
   c.native_permille = f.arith == SU3_ARITH_HYBRID ? 125 : 0;
   if (f.arith == SU3_ARITH_HYBRID) {
     c.block = 256;  // 8 warps, one of them native
-    if (f.layout == SU3_LAYOUT_AOS) c.tile_sites = 64;  // 256 links: one per thread and tile
+    if (f.layout == SU3_LAYOUT_AOS) {
+      c.tile_sites = 64;  // 256 links: one per thread and tile
+      c.stages = 3;       // two such CTAs fit in one SM's shared memory
+    }
   }
   return c;
 }

@@ -149,7 +149,10 @@ def test_hybrid_is_native_or_pair_per_site(layout, rep):
     hh = su3.Handle(0)
     V = 9 * 8 ** 3 + 7
     a, b = gen.lattice(11, V)
-    cfg = {"native_permille": 250}  # 2 of 8 warps: every 4th warp-tile runs natively
+    # 2 of 8 warps: every 4th warp-tile runs natively; AOS tiles of 64 sites keep all 8 warps busy
+    cfg = {"native_permille": 250, "block": 256}
+    if layout == su3.AOS:
+        cfg.update(tile_sites=64, stages=3, ctas_per_sm=2)
     got = run_form(hh, a, b, su3.F64, rep, rep, layout, arith=su3.HYBRID, cfg=cfg).reshape(V, 72)
     nat = run_form(hh, a, b, su3.F64, rep, rep, layout, arith=su3.NATIVE).reshape(V, 72)
     pair = run_form(hh, a, b, su3.F64, rep, rep, layout, arith=su3.F32PAIR).reshape(V, 72)
