@@ -48,27 +48,33 @@ def L48():
     return a, b, oracle.mult(a, b)
 
 
-@pytest.mark.parametrize("dtype,arith", [(su3.F64, su3.NATIVE), (su3.F64, su3.F32PAIR), (su3.F16, su3.NATIVE),
-                                         (su3.BF16, su3.NATIVE), (su3.F32, su3.NATIVE)],
-                         ids=["f64", "f64-f32pair", "f16", "bf16", "f32"])
-def test_L64_sampled(h, dtype, arith):
-    """L=64 (16.7M sites): the whole lattice runs on the GPU; 65,536 random sites are recomputed by
-    the oracle from the same generator and compared element by element."""
+@pytest.mark.parametrize("dtype,arith,rep,layout", [
+    (su3.F64, su3.NATIVE, su3.FULL18, su3.AOS), (su3.F64, su3.F32PAIR, su3.FULL18, su3.AOS),
+    (su3.F16, su3.NATIVE, su3.FULL18, su3.AOS), (su3.BF16, su3.NATIVE, su3.FULL18, su3.AOS),
+    (su3.F32, su3.NATIVE, su3.FULL18, su3.AOS), (su3.F64, su3.NATIVE, su3.FULL18, su3.SOA),
+    (su3.F64, su3.F32PAIR, su3.FULL18, su3.AOSOA32), (su3.F16, su3.NATIVE, su3.FULL18, su3.AOSOA32),
+    (su3.F64, su3.F32PAIR, su3.TWOROW12, su3.AOS), (su3.F32, su3.NATIVE, su3.TWOROW12, su3.AOS)],
+    ids=["f64", "f64-f32pair", "f16", "bf16", "f32", "f64-soa", "f64-f32pair-aosoa32", "f16-aosoa32",
+         "f64-f32pair-2row", "f32-2row"])
+def test_L64_sampled(h, dtype, arith, rep, layout):
+    """L=64 (16.7M sites, every array past 2^32 bytes for FP64): the whole lattice runs on the GPU;
+    65,536 random sites are recomputed by the oracle from the same generator and compared element
+    by element."""
     import torch
     V = 64 ** 4
     a = gen.sites(gen.DEFAULT_SEED, 0, V)
     b = gen.bmat(gen.DEFAULT_SEED, 0, V)
     a_dev = torch.from_numpy(a).cuda()
     del a
-    d = su3.Desc(dtype, su3.FULL18, su3.AOS, V, 0, arith)
-    if dtype == su3.F64:
+    d = su3.Desc(dtype, rep, layout, V, 0, arith)
+    if dtype == su3.F64 and rep == su3.FULL18 and layout == su3.AOS:
         abuf = a_dev
     else:
         abuf = torch.empty(su3.array_bytes(d), dtype=torch.uint8, device="cuda")
         h.pack(a_dev, d, abuf)
     cbuf = torch.empty(su3.array_bytes(d), dtype=torch.uint8, device="cuda")
     h.mult(d, abuf, b, d, cbuf)
-    out = a_dev if dtype != su3.F64 else torch.empty_like(a_dev)
+    out = a_dev if abuf is not a_dev else torch.empty_like(a_dev)
     h.unpack(d, cbuf, out)
     h.sync()
     idx = np.sort(np.random.default_rng(64).choice(V, 65536, replace=False))
@@ -76,7 +82,7 @@ def test_L64_sampled(h, dtype, arith):
     got = out.view(V, 72)[torch.from_numpy(idx).cuda()].cpu().numpy()
     ref = oracle.mult_sites(gen.sites_at(gen.DEFAULT_SEED, 0, idx), b)
     mx, rms = oracle.error(got, ref)
-    assert mx <= tol(dtype, su3.FULL18), (mx, rms)
+    assert mx <= tol(dtype, rep), (mx, rms)
 
 
 def test_every_bench_form_under_tuned_configs(h):
