@@ -297,6 +297,7 @@ su3_status su3_get_launch_cfg(su3_handle* h, const su3_desc* form, su3_launch_cf
   f.dtype = form->dtype;
   f.repr_in = f.repr_out = form->repr;
   f.layout = form->layout;
+  f.arith = form->arith;
   f.n_sites = form->n_sites;
   f.a_stride = f.c_stride = resolved_stride(form);
   LaunchCfg c = cfg_for(h, form, f);

@@ -132,6 +132,16 @@ def test_invalid_arguments_rejected(h):
     h.sync()
 
 
+def test_default_launch_cfg_reported_per_arithmetic():
+    """su3_get_launch_cfg on a fresh handle reports the default each arithmetic actually runs with."""
+    h = su3.Handle(0)
+    nat = h.get_launch_cfg(su3.Desc(su3.F64, su3.FULL18, su3.AOS, 10, 0, su3.NATIVE))
+    hyb = h.get_launch_cfg(su3.Desc(su3.F64, su3.FULL18, su3.AOS, 10, 0, su3.HYBRID))
+    assert nat["native_permille"] == 0
+    assert hyb["native_permille"] == 125 and hyb["block"] == 256 and hyb["tile_sites"] == 64 and hyb["stages"] == 3
+    h.close()
+
+
 def test_launch_cfg_variants_agree():
     """Every tile size / stage depth / block gives the same bits (sites are independent)."""
     h = su3.Handle(0)  # its own handle: the configurations below stay local to it
