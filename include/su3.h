@@ -97,10 +97,12 @@ typedef struct su3_handle su3_handle;
 
 /* Launch configuration of the streaming kernels (for the autotuner); 0 fields = default. */
 typedef struct {
-  int32_t block;        /* threads per CTA (multiple of 32, <= 1024) */
-  int32_t tile_sites;   /* AOS: sites per shared-memory tile; others: links per thread x 32 */
+  int32_t block;        /* threads per CTA: a multiple of 32 in [32, 256] */
+  int32_t tile_sites;   /* AOS: sites per shared-memory tile (1..1024, at most 1 MiB; shrunk at launch
+                           until ctas_per_sm CTAs fit in one SM's shared memory);
+                           AOSOA32/SOA: links per thread (1, 2 or 4) */
   int32_t stages;       /* AOS: shared-memory pipeline depth (2..8) */
-  int32_t ctas_per_sm;  /* CTAs per SM in the persistent grid */
+  int32_t ctas_per_sm;  /* CTAs per SM in the persistent grid (1..32) */
   int32_t native_permille;  /* HYBRID only: share of each CTA's warps computing natively, 1/1000 */
 } su3_launch_cfg;
 

@@ -23,6 +23,29 @@ def test_library_exports_header():
     assert L.su3_abi_version() == 1
 
 
+def test_header_is_plain_c_and_links(tmp_path):
+    """include/su3.h compiles as strict C99 and a C caller links against libsu3 (no torch types)."""
+    src = tmp_path / "caller.c"
+    src.write_text(
+        '#include "su3.h"\n'
+        "int run(const void* a, void* c, void* stream, long long n) {\n"
+        "  double b[4][3][3][2] = {{{{0}}}};\n"
+        "  su3_handle* h;\n"
+        "  if (su3_init(0, &h) != SU3_OK) return 1;\n"
+        "  su3_desc d = {SU3_F64, SU3_REPR_FULL18, SU3_LAYOUT_AOS, SU3_ARITH_NATIVE, n, 0};\n"
+        "  su3_status s = su3_mult(h, &d, a, &b[0][0][0][0], &d, c, stream);\n"
+        "  if (s == SU3_OK) s = su3_sync(h, stream, -1);\n"
+        "  su3_finalize(h);\n"
+        "  return (int)s;\n"
+        "}\n")
+    lib = su3.library_path()
+    out = tmp_path / "caller.so"
+    r = subprocess.run(["gcc", "-std=c99", "-Wall", "-Werror", "-pedantic", "-shared", "-fPIC", "-I",
+                        os.path.join(ROOT, "include"), str(src), "-o", str(out), "-L", os.path.dirname(lib),
+                        "-lsu3"], capture_output=True, text=True)
+    assert r.returncode == 0, r.stderr
+
+
 def test_status_strings():
     L = su3.lib()
     for s, name in enumerate(["SU3_OK", "SU3_ERR_INVALID_ARG", "SU3_ERR_UNSUPPORTED", "SU3_ERR_CUDA",
