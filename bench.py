@@ -506,34 +506,37 @@ def adjacent_leg(h, torch, su3, a_dev, b, V, stream, extra, V_sample, reps=10):
 
 def e2e_leg(h, torch, su3, a_host, b, V, args, stream, world, dev, a_dev=None, c_dev=None):
     """The same step through the host-buffer entry point: H2D of a from pinned memory, the kernel,
-    D2H of c, all inside the timed region (chunked and overlapped inside libsu3). For context, the
-    same bytes are then moved by two plain concurrent copies with no kernel (what the host link
-    gives on this machine at this moment: it varies from machine to machine)."""
+    D2H of c, all inside the timed region (chunked and overlapped inside libsu3). For context, each
+    step is followed by the same bytes moved by two plain concurrent copies with no kernel, timed
+    separately: what the host link gives at that moment (it varies with load from other tenants)."""
     d64 = su3.Desc(su3.F64, su3.FULL18, su3.AOS, V)
     c_host = torch.empty(V * 72, dtype=torch.float64, pin_memory=True)
     h.mult_host(d64, a_host.data_ptr(), b, d64, c_host.data_ptr(), stream)  # warm (staging buffers)
     k = max(3, min(args.steps, 5))
+    copies = a_dev is not None and c_dev is not None
+    s_in, s_out = (torch.cuda.Stream(), torch.cuda.Stream()) if copies else (None, None)
+    el = cel = 0.0
     barrier(world)
-    t0 = time.perf_counter()
     for _ in range(k):
+        t0 = time.perf_counter()
         h.mult_host(d64, a_host.data_ptr(), b, d64, c_host.data_ptr(), stream)
-    el = time.perf_counter() - t0
+        el += time.perf_counter() - t0
+        if copies:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            with torch.cuda.stream(s_in):
+                c_dev.copy_(a_host, non_blocking=True)
+            with torch.cuda.stream(s_out):
+                c_host.copy_(a_dev, non_blocking=True)
+            torch.cuda.synchronize()
+            cel += time.perf_counter() - t0
     el = max_over_ranks(el, world, dev)
     gbs = world * 1152.0 * V * k / el / 1e9
     out = {"value": round(gbs, 2), "unit": "GB/s", "h2d_bytes_per_step": 576 * V, "d2h_bytes_per_step": 576 * V,
            "steps": k, "ms_per_step": round(el / k * 1e3, 3),
            "api": "su3_mult_host (pinned host a and c; chunked H2D / kernel / D2H overlapped on 3 streams)"}
-    if a_dev is not None and c_dev is not None:
-        s_in, s_out = torch.cuda.Stream(), torch.cuda.Stream()
-        torch.cuda.synchronize()
-        t0 = time.perf_counter()
-        for _ in range(k):
-            with torch.cuda.stream(s_in):
-                c_dev.copy_(a_host, non_blocking=True)
-            with torch.cuda.stream(s_out):
-                c_host.copy_(a_dev, non_blocking=True)
-        torch.cuda.synchronize()
-        cel = max_over_ranks(time.perf_counter() - t0, world, dev)
+    if copies:
+        cel = max_over_ranks(cel, world, dev)
         out["copies_only_GBps"] = round(world * 1152.0 * V * k / cel / 1e9, 2)
         out["vs_copies_only"] = round(gbs / out["copies_only_GBps"], 3)
     del c_host
