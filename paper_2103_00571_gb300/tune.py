@@ -138,18 +138,22 @@ def tune_forms(h, names, L=48, log=print):
     return results
 
 
-def tune_batched(h, log=print):
+def make_batch96(h, arith=None):
+    """The 96-lattice workload: extents drawn from {4, 6, ..., 24}, FP64 (even index) / FP32 (odd),
+    each lattice with its own b. FP64 lattices take ``arith`` (default NATIVE). Returns the batch
+    items and the device buffers that must stay alive while they are used."""
     import ctypes
 
     import torch
 
     import su3_inputs as gen
+    arith = B.NATIVE if arith is None else arith
     ext = gen.extents(gen.DEFAULT_SEED, 96)
     items, keep = [], []
     for k in range(96):
         V = int(np.prod(ext[k]))
         dt = B.F64 if k % 2 == 0 else B.F32
-        d = B.Desc(dt, B.FULL18, B.AOS, V)
+        d = B.Desc(dt, B.FULL18, B.AOS, V, 0, arith if dt == B.F64 else B.NATIVE)
         a = torch.from_numpy(gen.sites(gen.DEFAULT_SEED, k, V)).cuda()
         abuf = torch.empty(B.array_bytes(d), dtype=torch.uint8, device="cuda")
         h.pack(a, d, abuf)
@@ -157,23 +161,36 @@ def tune_batched(h, log=print):
         keep += [abuf, cbuf]
         items.append(B.BatchItem(d, abuf.data_ptr(), cbuf.data_ptr(),
                                  (ctypes.c_double * 72)(*gen.bmat(gen.DEFAULT_SEED, k, V))))
+    h.sync()
+    return items, keep
+
+
+def time_batched(h, items, reps=10, warm=3):
+    """Mean ms of one graph-replayed batched launch (CUDA events on the current stream)."""
+    import torch
+    s = torch.cuda.current_stream()
+    for _ in range(warm):
+        h.mult_batched(items, s, use_graph=True)
+    h.sync()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(s)
+    for _ in range(reps):
+        h.mult_batched(items, s, use_graph=True)
+    e1.record(s)
+    e1.synchronize()
+    h.sync()
+    return e0.elapsed_time(e1) / reps
+
+
+def tune_batched(h, log=print):
+    items, keep = make_batch96(h)
     best = None
     for block, ts, stages, cps in itertools.product((64, 128, 256), (16, 32, 64), (2, 3, 4), (1, 2, 3, 4, 6)):
         if 1024 + stages * ((ts * 576 + 127) // 128 * 128) > 227 * 1024 // cps or block * cps > 1024:
             continue
         cfg = dict(block=block, tile_sites=ts, stages=stages, ctas_per_sm=cps)
         h.set_batched_cfg(**cfg)
-        for _ in range(3):
-            h.mult_batched(items, use_graph=True)
-        h.sync()
-        s = torch.cuda.current_stream()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(s)
-        for _ in range(10):
-            h.mult_batched(items, use_graph=True)
-        e1.record(s)
-        e1.synchronize()
-        ms = e0.elapsed_time(e1) / 10
+        ms = time_batched(h, items)
         if best is None or ms < best[0]:
             best = (ms, cfg)
     h.set_batched_cfg(**best[1])
@@ -187,8 +204,20 @@ def main():
     ap.add_argument("--forms", default="all")
     ap.add_argument("--batched", action="store_true")
     ap.add_argument("--out", default=CACHE)
+    ap.add_argument("--time-batched", type=int, default=0, metavar="REPS",
+                    help="only time the 96-lattice batch under the cached configuration (REPS graph replays)")
+    ap.add_argument("--arith", default="native", choices=["native", "f32pair"],
+                    help="arithmetic of the FP64 lattices for --time-batched")
     args = ap.parse_args()
     h = B.Handle(0)
+    if args.time_batched:
+        apply_cached(h)
+        items, keep = make_batch96(h, AR[args.arith])
+        ms = time_batched(h, items, reps=args.time_batched)
+        sites = sum(it.desc.n_sites for it in items)
+        print(json.dumps({"workload": "96-lattice batch", "arith": args.arith, "ms": round(ms, 4),
+                          "site_updates_per_s": round(sites / (ms * 1e-3), 1), "cfg": h.get_batched_cfg()}))
+        return
     names = ALL_FORMS if args.forms == "all" else args.forms.split(",")
     cache = load_cache()
     key = gpu_key()
