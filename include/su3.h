@@ -28,7 +28,7 @@
 extern "C" {
 #endif
 
-#define SU3_ABI_VERSION 1
+#define SU3_ABI_VERSION 2
 
 typedef enum {
   SU3_OK = 0,
@@ -104,6 +104,10 @@ typedef struct {
   int32_t stages;       /* AOS: shared-memory pipeline depth (2..8) */
   int32_t ctas_per_sm;  /* CTAs per SM in the persistent grid (1..32) */
   int32_t native_permille;  /* HYBRID only: share of each CTA's warps computing natively, 1/1000 */
+  int32_t threads_per_link; /* AOS: 1 = one thread computes a whole link (default); 3 = one thread
+                               per output row (row split: three threads per link, two for TWOROW12
+                               output). su3_mult_op SU3_OP_AN and su3_mat_vec always use 1. Other
+                               layouts: 1. su3_set_batched_cfg: 1 or 3. */
 } su3_launch_cfg;
 
 /* One lattice of a batched call. a/c are device pointers; b as in su3_mult. */

@@ -48,7 +48,8 @@ class Desc(ctypes.Structure):
 
 class LaunchCfg(ctypes.Structure):
     _fields_ = [("block", ctypes.c_int32), ("tile_sites", ctypes.c_int32), ("stages", ctypes.c_int32),
-                ("ctas_per_sm", ctypes.c_int32), ("native_permille", ctypes.c_int32)]
+                ("ctas_per_sm", ctypes.c_int32), ("native_permille", ctypes.c_int32),
+                ("threads_per_link", ctypes.c_int32)]
 
     def as_dict(self):
         return {k: getattr(self, k) for k, _ in self._fields_}
@@ -236,7 +237,7 @@ class Handle:
 
     def set_launch_cfg(self, form, **cfg):
         c = LaunchCfg(cfg.get("block", 0), cfg.get("tile_sites", 0), cfg.get("stages", 0), cfg.get("ctas_per_sm", 0),
-                      cfg.get("native_permille", 0))
+                      cfg.get("native_permille", 0), cfg.get("threads_per_link", 0))
         self._check(lib().su3_set_launch_cfg(self._h, ctypes.byref(form), ctypes.byref(c)), "su3_set_launch_cfg")
 
     def get_launch_cfg(self, form):
@@ -245,7 +246,8 @@ class Handle:
         return c.as_dict()
 
     def set_batched_cfg(self, **cfg):
-        c = LaunchCfg(cfg.get("block", 0), cfg.get("tile_sites", 0), cfg.get("stages", 0), cfg.get("ctas_per_sm", 0))
+        c = LaunchCfg(cfg.get("block", 0), cfg.get("tile_sites", 0), cfg.get("stages", 0), cfg.get("ctas_per_sm", 0),
+                      0, cfg.get("threads_per_link", 0))
         self._check(lib().su3_set_batched_cfg(self._h, ctypes.byref(c)), "su3_set_batched_cfg")
 
     def get_batched_cfg(self):

@@ -112,12 +112,16 @@ su3_status check_cfg(su3_handle* h, const Form& f, const LaunchCfg& c) {
   if (c.native_permille < 0 || c.native_permille > 1000)
     return fail(h, SU3_ERR_INVALID_ARG, "native_permille must be in [0, 1000]");
   if (f.layout == SU3_LAYOUT_AOS) {
+    if (c.threads_per_link != 1 && c.threads_per_link != 3)
+      return fail(h, SU3_ERR_INVALID_ARG, "threads_per_link must be 1 (per link) or 3 (one thread per output row)");
     if (c.stages < 2 || c.stages > 8) return fail(h, SU3_ERR_INVALID_ARG, "stages must be in [2, 8]");
     if (c.tile_sites < 1 || c.tile_sites > 1024) return fail(h, SU3_ERR_INVALID_ARG, "tile_sites must be in [1, 1024]");
     if ((int64_t)c.tile_sites * f.a_stride > (1 << 20))
       return fail(h, SU3_ERR_INVALID_ARG, "a tile may not exceed 1 MiB");
   } else if (c.tile_sites != 1 && c.tile_sites != 2 && c.tile_sites != 4) {
     return fail(h, SU3_ERR_INVALID_ARG, "links per thread (tile_sites) must be 1, 2 or 4 for SOA/AOSOA32");
+  } else if (c.threads_per_link != 1) {
+    return fail(h, SU3_ERR_INVALID_ARG, "threads_per_link must be 1 for SOA/AOSOA32");
   }
   return SU3_OK;
 }
@@ -284,6 +288,7 @@ su3_status su3_set_launch_cfg(su3_handle* h, const su3_desc* form, const su3_lau
   if (cfg->stages) c.stages = cfg->stages;
   if (cfg->ctas_per_sm) c.ctas_per_sm = cfg->ctas_per_sm;
   if (cfg->native_permille) c.native_permille = cfg->native_permille;
+  if (cfg->threads_per_link) c.threads_per_link = cfg->threads_per_link;
   su3_status s = check_cfg(h, f, c);
   if (s != SU3_OK) return s;
   h->cfgs[form_key(form)] = c;
@@ -306,6 +311,7 @@ su3_status su3_get_launch_cfg(su3_handle* h, const su3_desc* form, su3_launch_cf
   cfg->stages = c.stages;
   cfg->ctas_per_sm = c.ctas_per_sm;
   cfg->native_permille = c.native_permille;
+  cfg->threads_per_link = c.threads_per_link;
   return SU3_OK;
 }
 
@@ -317,10 +323,12 @@ su3_status su3_set_batched_cfg(su3_handle* h, const su3_launch_cfg* cfg) {
   if (cfg->tile_sites) c.tile_sites = cfg->tile_sites;
   if (cfg->stages) c.stages = cfg->stages;
   if (cfg->ctas_per_sm) c.ctas_per_sm = cfg->ctas_per_sm;
+  if (cfg->threads_per_link) c.threads_per_link = cfg->threads_per_link;
   if (c.block < 32 || c.block > 256 || c.block % 32 || c.stages < 2 || c.stages > 8 || c.tile_sites < 1 ||
-      c.tile_sites > 256 || c.ctas_per_sm < 1 || c.ctas_per_sm > 32)
+      c.tile_sites > 256 || c.ctas_per_sm < 1 || c.ctas_per_sm > 32 ||
+      (c.threads_per_link != 1 && c.threads_per_link != 3))
     return fail(h, SU3_ERR_INVALID_ARG, "batched cfg out of range (block 32..256 step 32, stages 2..8, "
-                                        "tile_sites 1..256, ctas_per_sm 1..32)");
+                                        "tile_sites 1..256, ctas_per_sm 1..32, threads_per_link 1 or 3)");
   h->bcfg = c;
   h->gkey.clear();  // the next graph-mode call captures a new graph
   return SU3_OK;
@@ -334,6 +342,7 @@ su3_status su3_get_batched_cfg(su3_handle* h, su3_launch_cfg* cfg) {
   cfg->stages = h->bcfg.stages;
   cfg->ctas_per_sm = h->bcfg.ctas_per_sm;
   cfg->native_permille = 0;
+  cfg->threads_per_link = h->bcfg.threads_per_link;
   return SU3_OK;
 }
 
@@ -397,6 +406,7 @@ su3_status su3_mult_op(su3_handle* h, int32_t op, const su3_desc* a_desc, const 
   }
   if (h->fault & kFaultLaunch) return fail(h, SU3_ERR_FAULT_INJECTED, "fault injected at launch");
   LaunchCfg cfg = cfg_for(h, a_desc, f);
+  cfg.threads_per_link = 1;  // row k of a^dagger b reads column k of a: no row split
   s = check_cfg(h, f, cfg);
   if (s != SU3_OK) return s;
   return launch_adjacent(0, f, cfg, a_dev, b, c_dev, ctx_of(h, (cudaStream_t)stream));
@@ -419,6 +429,7 @@ su3_status su3_mat_vec(su3_handle* h, int32_t adjoint, const su3_desc* a_desc, c
     return fail(h, SU3_ERR_INVALID_ARG, "a and w overlap");
   if (h->fault & kFaultLaunch) return fail(h, SU3_ERR_FAULT_INJECTED, "fault injected at launch");
   LaunchCfg cfg = cfg_for(h, a_desc, f);
+  cfg.threads_per_link = 1;  // one output vector per link
   s = check_cfg(h, f, cfg);
   if (s != SU3_OK) return s;
   double vb[72] = {0};

@@ -39,7 +39,17 @@ struct BatchArgs {
 
 constexpr int kBatchHeader = 1024;  // mbarriers (<= 8) + TileInfo per stage (<= 8 x 16 B)
 
-template <int DT>
+// Work item q of a tile with `links` links and TPL threads per link (1, or 3 = one per row): the
+// items are ordered row-major over (row, link), so an item's direction j = q % 4 = tid % 4.
+template <int TPL>
+__device__ __forceinline__ void batch_item(int q, int links, int& row, int& link) {
+  row = 0;
+  if (TPL >= 2 && q >= links) row = 1;
+  if (TPL >= 3 && q >= 2 * links) row = 2;
+  link = q - row * links;
+}
+
+template <int DT, int TPL>
 __device__ __forceinline__ void batch_tile_compute(unsigned char* in, int nt, const BatchDesc& d) {
   using S = Storage<DT>;
   using A = typename S::acc;
@@ -52,27 +62,45 @@ __device__ __forceinline__ void batch_tile_compute(unsigned char* in, int nt, co
     bre[e] = (A)__ldg(&d.b[18 * j + 2 * e]);
     bim[e] = (A)__ldg(&d.b[18 * j + 2 * e + 1]);
   }
-  for (int q = threadIdx.x; q < 4 * nt; q += blockDim.x) {
-    V* p = reinterpret_cast<V*>(in + (size_t)q * kLink);
-    Link<A> la, lc;
+  const int links = 4 * nt;
+  for (int q = threadIdx.x; q < TPL * links; q += blockDim.x) {
+    int row, link;
+    batch_item<TPL>(q, links, row, link);
+    V* p = reinterpret_cast<V*>(in + (size_t)link * kLink);
+    if constexpr (TPL == 1) {
+      Link<A> la, lc;
 #pragma unroll
-    for (int e = 0; e < 9; ++e) S::unpack(p[e], la.re[e], la.im[e]);
-    link_mult<3>(la, bre, bim, lc);
+      for (int e = 0; e < 9; ++e) S::unpack(p[e], la.re[e], la.im[e]);
+      link_mult<3>(la, bre, bim, lc);
 #pragma unroll
-    for (int e = 0; e < 9; ++e) p[e] = S::pack(lc.re[e], lc.im[e]);
+      for (int e = 0; e < 9; ++e) p[e] = S::pack(lc.re[e], lc.im[e]);
+    } else {
+      A are[3], aim[3], cre[3], cim[3];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) S::unpack(p[3 * row + m], are[m], aim[m]);
+      row_mult(are, aim, bre, bim, cre, cim);
+#pragma unroll
+      for (int l = 0; l < 3; ++l) p[3 * row + l] = S::pack(cre[l], cim[l]);
+    }
   }
 }
 
 // FP64 lattice in FP32-pair arithmetic: b comes pre-split in the descriptor.
+template <int TPL>
 __device__ __forceinline__ void batch_tile_compute_pair(unsigned char* in, int nt, const BatchDesc& d) {
   PairF64Op<9, 3> op;
   op.init_pre(d.bpair + 36 * (threadIdx.x & 3));
-  for (int q = threadIdx.x; q < 4 * nt; q += blockDim.x) {
-    double2* p = reinterpret_cast<double2*>(in + (size_t)q * 144);
-    op.apply(p, p);
+  const int links = 4 * nt;
+  for (int q = threadIdx.x; q < TPL * links; q += blockDim.x) {
+    int row, link;
+    batch_item<TPL>(q, links, row, link);
+    double2* p = reinterpret_cast<double2*>(in + (size_t)link * 144);
+    if constexpr (TPL == 1) op.apply(p, p);
+    else op.apply_row(p, p, row);
   }
 }
 
+template <int TPL>
 __global__ void __launch_bounds__(256) su3_batched_kernel(const __grid_constant__ BatchArgs p) {
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
@@ -136,10 +164,10 @@ __global__ void __launch_bounds__(256) su3_batched_kernel(const __grid_constant_
     const int dtype = d.dtype;
     if (ok) {
       if (dtype == SU3_F64) {
-        if (d.arith == SU3_ARITH_F32PAIR) batch_tile_compute_pair(in, ti.nt, d);
-        else batch_tile_compute<kF64>(in, ti.nt, d);
+        if (d.arith == SU3_ARITH_F32PAIR) batch_tile_compute_pair<TPL>(in, ti.nt, d);
+        else batch_tile_compute<kF64, TPL>(in, ti.nt, d);
       } else {
-        batch_tile_compute<kF32>(in, ti.nt, d);
+        batch_tile_compute<kF32, TPL>(in, ti.nt, d);
       }
     }
     fence_proxy_async_smem();
@@ -193,7 +221,12 @@ su3_status prepare_batched(const BatchCfg& cfg, std::string* err) {
     *err = "batched launch configuration exceeds shared memory, stage or block limits";
     return SU3_ERR_INVALID_ARG;
   }
-  cudaError_t e = cudaFuncSetAttribute(su3_batched_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (cfg.threads_per_link != 1 && cfg.threads_per_link != 3) {
+    *err = "batched threads_per_link must be 1 or 3";
+    return SU3_ERR_INVALID_ARG;
+  }
+  cudaError_t e = cudaFuncSetAttribute(cfg.threads_per_link == 3 ? su3_batched_kernel<3> : su3_batched_kernel<1>,
+                                       cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) {
     *err = std::string("cudaFuncSetAttribute: ") + cudaGetErrorString(e);
     return SU3_ERR_CUDA;
@@ -221,7 +254,8 @@ su3_status launch_batched(const BatchDesc* descs_dev, int n, int total_tiles, co
   }
   cudaError_t e;
   const int grid = std::min(total_tiles, ctx.num_sms * cfg.ctas_per_sm);
-  su3_batched_kernel<<<grid, cfg.block, smem, ctx.stream>>>(p);
+  if (cfg.threads_per_link == 3) su3_batched_kernel<3><<<grid, cfg.block, smem, ctx.stream>>>(p);
+  else su3_batched_kernel<1><<<grid, cfg.block, smem, ctx.stream>>>(p);
   e = cudaGetLastError();
   if (e != cudaSuccess) {
     *ctx.err = std::string("su3_batched_kernel launch: ") + cudaGetErrorString(e);

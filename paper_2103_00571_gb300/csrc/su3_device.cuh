@@ -200,47 +200,84 @@ struct Link {
 };
 
 // Row 2 of an SU(3) matrix from rows 0 and 1: conj(row0 x row1), with
-// (u x v)_k = u_p v_q - u_q v_p, (p, q) = (k+1, k+2) mod 3.
+// (u x v)_k = u_p v_q - u_q v_p, (p, q) = (k+1, k+2) mod 3. r0/r1 hold rows 0 and 1 (re, im).
 template <typename T>
-__device__ __forceinline__ void rebuild_row2(Link<T>& a) {
+__device__ __forceinline__ void rebuild_row2_elems(const T (&r0re)[3], const T (&r0im)[3], const T (&r1re)[3],
+                                                   const T (&r1im)[3], T (&ore)[3], T (&oim)[3]) {
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const int p = (k + 1) % 3, q = (k + 2) % 3;
-    T xr = a.re[p] * a.re[3 + q];
-    xr = fma(-a.im[p], a.im[3 + q], xr);
-    xr = fma(-a.re[q], a.re[3 + p], xr);
-    xr = fma(a.im[q], a.im[3 + p], xr);
-    T xi = a.re[p] * a.im[3 + q];
-    xi = fma(a.im[p], a.re[3 + q], xi);
-    xi = fma(-a.re[q], a.im[3 + p], xi);
-    xi = fma(-a.im[q], a.re[3 + p], xi);
-    a.re[6 + k] = xr;
-    a.im[6 + k] = -xi;
+    T xr = r0re[p] * r1re[q];
+    xr = fma(-r0im[p], r1im[q], xr);
+    xr = fma(-r0re[q], r1re[p], xr);
+    xr = fma(r0im[q], r1im[p], xr);
+    T xi = r0re[p] * r1im[q];
+    xi = fma(r0im[p], r1re[q], xi);
+    xi = fma(-r0re[q], r1im[p], xi);
+    xi = fma(-r0im[q], r1re[p], xi);
+    ore[k] = xr;
+    oim[k] = -xi;
   }
 }
 
-// c[k][l] = sum_m a[k][m] b[m][l] for rows k < ROWS (the SU3_Bench kernel's inner k, l, m loops;
+template <typename T>
+__device__ __forceinline__ void rebuild_row2(Link<T>& a) {
+  T r0re[3], r0im[3], r1re[3], r1im[3], ore[3], oim[3];
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    r0re[m] = a.re[m];
+    r0im[m] = a.im[m];
+    r1re[m] = a.re[3 + m];
+    r1im[m] = a.im[3 + m];
+  }
+  rebuild_row2_elems(r0re, r0im, r1re, r1im, ore, oim);
+#pragma unroll
+  for (int m = 0; m < 3; ++m) {
+    a.re[6 + m] = ore[m];
+    a.im[6 + m] = oim[m];
+  }
+}
+
+// One output row: c[l] = sum_m a[m] b[m][l] (the SU3_Bench kernel's inner l, m loops for one k;
 // 4 real FMAs per complex multiply-accumulate).
+template <typename T>
+__device__ __forceinline__ void row_mult(const T (&are)[3], const T (&aim)[3], const T (&bre)[9], const T (&bim)[9],
+                                         T (&cre)[3], T (&cim)[3]) {
+#pragma unroll
+  for (int l = 0; l < 3; ++l) {
+    T re = are[0] * bre[l];
+    T im = are[0] * bim[l];
+    re = fma(-aim[0], bim[l], re);
+    im = fma(aim[0], bre[l], im);
+#pragma unroll
+    for (int m = 1; m < 3; ++m) {
+      re = fma(are[m], bre[3 * m + l], re);
+      re = fma(-aim[m], bim[3 * m + l], re);
+      im = fma(are[m], bim[3 * m + l], im);
+      im = fma(aim[m], bre[3 * m + l], im);
+    }
+    cre[l] = re;
+    cim[l] = im;
+  }
+}
+
+// c[k][l] = sum_m a[k][m] b[m][l] for rows k < ROWS.
 template <int ROWS, typename T>
 __device__ __forceinline__ void link_mult(const Link<T>& a, const T (&bre)[9], const T (&bim)[9],
                                           Link<T>& c) {
 #pragma unroll
   for (int k = 0; k < ROWS; ++k) {
+    T are[3], aim[3], cre[3], cim[3];
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      are[m] = a.re[3 * k + m];
+      aim[m] = a.im[3 * k + m];
+    }
+    row_mult(are, aim, bre, bim, cre, cim);
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
-      T re = a.re[3 * k] * bre[l];
-      T im = a.re[3 * k] * bim[l];
-      re = fma(-a.im[3 * k], bim[l], re);
-      im = fma(a.im[3 * k], bre[l], im);
-#pragma unroll
-      for (int m = 1; m < 3; ++m) {
-        re = fma(a.re[3 * k + m], bre[3 * m + l], re);
-        re = fma(-a.im[3 * k + m], bim[3 * m + l], re);
-        im = fma(a.re[3 * k + m], bim[3 * m + l], im);
-        im = fma(a.im[3 * k + m], bre[3 * m + l], im);
-      }
-      c.re[3 * k + l] = re;
-      c.im[3 * k + l] = im;
+      c.re[3 * k + l] = cre[l];
+      c.im[3 * k + l] = cim[l];
     }
   }
 }
@@ -256,6 +293,7 @@ struct NativeOp {
   using V = typename S::vec;
   using BArg = A;              // precision of b in the kernel parameters
   static constexpr int kNeIn = NE_IN, kNeOut = 3 * ROWS_OUT;
+  static constexpr bool kRowSplit = true;  // has apply_row: one thread per output row is possible
   A bre[9], bim[9];
   __device__ __forceinline__ void begin_tile(int) {}
   __device__ __forceinline__ void init(const BArg* bj, int /*native_warps*/) {
@@ -274,6 +312,26 @@ struct NativeOp {
 #pragma unroll
     for (int e = 0; e < 3 * ROWS_OUT; ++e) dst[e] = S::pack(lc.re[e], lc.im[e]);
   }
+  // Output row k alone (row split: one thread per output row). Reads input row k only, except
+  // that a rebuilt row 2 reads rows 0 and 1; the arithmetic is exactly that of apply().
+  __device__ __forceinline__ void apply_row(const V* src, V* dst, int k) const {
+    A are[3], aim[3], cre[3], cim[3];
+    if (NE_IN == 6 && ROWS_OUT == 3 && k == 2) {
+      A r0re[3], r0im[3], r1re[3], r1im[3];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        S::unpack(src[m], r0re[m], r0im[m]);
+        S::unpack(src[3 + m], r1re[m], r1im[m]);
+      }
+      rebuild_row2_elems(r0re, r0im, r1re, r1im, are, aim);
+    } else {
+#pragma unroll
+      for (int m = 0; m < 3; ++m) S::unpack(src[3 * k + m], are[m], aim[m]);
+    }
+    row_mult(are, aim, bre, bim, cre, cim);
+#pragma unroll
+    for (int l = 0; l < 3; ++l) dst[3 * k + l] = S::pack(cre[l], cim[l]);
+  }
 };
 
 // ---- adjacent SU(3) operations ----------------------------------------------------------------
@@ -289,6 +347,7 @@ struct AnOp {  // c[k][l] = sum_m conj(a[m][k]) b[m][l]
   using V = typename S::vec;
   using BArg = A;
   static constexpr int kNeIn = 9, kNeOut = 9;
+  static constexpr bool kRowSplit = false;  // row k of a^dagger b reads column k of a
   A bre[9], bim[9];
   __device__ __forceinline__ void begin_tile(int) {}
   __device__ __forceinline__ void init(const BArg* bj, int) {
@@ -331,6 +390,7 @@ struct MatVecOp {  // w[k] = sum_m a[k][m] v[m]   (ADJ: sum_m conj(a[m][k]) v[m]
   using V = typename S::vec;
   using BArg = A;
   static constexpr int kNeIn = 9, kNeOut = 3;
+  static constexpr bool kRowSplit = false;  // one output vector per link
   A vre[3], vim[3];
   __device__ __forceinline__ void begin_tile(int) {}
   __device__ __forceinline__ void init(const BArg* vj, int) {
@@ -450,6 +510,7 @@ struct PairF64Op {
   using V = double2;
   using BArg = double;
   static constexpr int kNeIn = NE_IN, kNeOut = 3 * ROWS_OUT;
+  static constexpr bool kRowSplit = true;
   // b[j] split once per thread, as lane pairs for the two terms of each (m, l):
   // (re, im) lanes of ar*(br, bi) and of ai*(-bi, br), high and low parts.
   float2 ya[9], yb[9], yla[9], ylb[9];
@@ -478,33 +539,35 @@ struct PairF64Op {
       ylb[e] = make_float2(-il, rl);
     }
   }
-  __device__ __forceinline__ void apply(const V* src, V* dst) const {
+  // Output row k: reads input row k and writes output row k (so src and dst may alias).
+  __device__ __forceinline__ void apply_row(const V* src, V* dst, int k) const {
     static_assert(NE_IN == 9 || ROWS_OUT == 2, "F32PAIR rebuilds no row 2");
+    float xh[6], xl[6];  // terms 2m: a_re[k][m], 2m+1: a_im[k][m]
 #pragma unroll
-    for (int k = 0; k < ROWS_OUT; ++k) {
-      float xh[6], xl[6];  // terms 2m: a_re[k][m], 2m+1: a_im[k][m]
+    for (int m = 0; m < 3; ++m) {
+      const double2 v = src[3 * k + m];
+      const FF r = split_f64(v.x), i = split_f64(v.y);
+      xh[2 * m] = r.h;
+      xl[2 * m] = r.l;
+      xh[2 * m + 1] = i.h;
+      xl[2 * m + 1] = i.l;
+    }
+#pragma unroll
+    for (int l = 0; l < 3; ++l) {
+      float2 yh[6], yl[6];
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
-        const double2 v = src[3 * k + m];
-        const FF r = split_f64(v.x), i = split_f64(v.y);
-        xh[2 * m] = r.h;
-        xl[2 * m] = r.l;
-        xh[2 * m + 1] = i.h;
-        xl[2 * m + 1] = i.l;
+        yh[2 * m] = ya[3 * m + l];
+        yl[2 * m] = yla[3 * m + l];
+        yh[2 * m + 1] = yb[3 * m + l];
+        yl[2 * m + 1] = ylb[3 * m + l];
       }
-#pragma unroll
-      for (int l = 0; l < 3; ++l) {
-        float2 yh[6], yl[6];
-#pragma unroll
-        for (int m = 0; m < 3; ++m) {
-          yh[2 * m] = ya[3 * m + l];
-          yl[2 * m] = yla[3 * m + l];
-          yh[2 * m + 1] = yb[3 * m + l];
-          yl[2 * m + 1] = ylb[3 * m + l];
-        }
-        dst[3 * k + l] = dot6_pair2(xh, xl, yh, yl);
-      }
+      dst[3 * k + l] = dot6_pair2(xh, xl, yh, yl);
     }
+  }
+  __device__ __forceinline__ void apply(const V* src, V* dst) const {
+#pragma unroll
+    for (int k = 0; k < ROWS_OUT; ++k) apply_row(src, dst, k);
   }
 };
 
@@ -517,6 +580,7 @@ struct HybridF64Op {
   using V = double2;
   using BArg = double;
   static constexpr int kNeIn = NE_IN, kNeOut = 3 * ROWS_OUT;
+  static constexpr bool kRowSplit = true;
   NativeOp<kF64, NE_IN, ROWS_OUT> nat;
   PairF64Op<NE_IN, ROWS_OUT> pair;
   int period;  // 0: never native
@@ -534,6 +598,10 @@ struct HybridF64Op {
   __device__ __forceinline__ void apply(const V* src, V* dst) const {
     if (native) nat.apply(src, dst);
     else pair.apply(src, dst);
+  }
+  __device__ __forceinline__ void apply_row(const V* src, V* dst, int k) const {
+    if (native) nat.apply_row(src, dst, k);
+    else pair.apply_row(src, dst, k);
   }
 };
 

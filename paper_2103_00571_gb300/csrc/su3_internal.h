@@ -30,6 +30,7 @@ struct LaunchCfg {
   int stages;
   int ctas_per_sm;
   int native_permille;  // HYBRID: share of tiles on the FP64 pipe
+  int threads_per_link = 1;  // AOS: 1, or 3 = one thread per output row (2 per link for two-row output)
 };
 
 // Everything a launcher needs from the handle.
@@ -95,6 +96,7 @@ struct BatchCfg {
   int tile_sites;
   int stages;
   int ctas_per_sm;
+  int threads_per_link = 1;  // 1, or 3: one thread per output row
 };
 
 BatchCfg default_batch_cfg();

@@ -60,7 +60,10 @@ __device__ __forceinline__ void load_b_op(const BMat<typename Op::BArg>& b, type
 // The AOS streaming kernel. Op::kNeIn complex elements per input link (9 full, 6 two-row),
 // Op::kNeOut per output link. In place (kNeOut == kNeIn): the result overwrites the input tile in
 // shared memory. Otherwise (two-row in, full out) results go to a ring of 3 output buffers.
-template <class Op>
+// TPL threads per link: 1 (a thread computes whole links), or one thread per output row. The work
+// items of a tile are then ordered row-major over (row, link), so that item q's link direction is
+// still q % 4 = tid % 4 and each thread keeps one b[j] in registers.
+template <class Op, int TPL>
 __global__ void __launch_bounds__(256) su3_aos_kernel(const __grid_constant__ AosArgs<typename Op::BArg> p) {
   using V = typename Op::V;
   using BA = typename Op::BArg;
@@ -119,11 +122,17 @@ __global__ void __launch_bounds__(256) su3_aos_kernel(const __grid_constant__ Ao
     unsigned char* out = kInPlace ? in : out0 + (size_t)(k % 3) * p.out_bytes;
     if (ok) {
       op.begin_tile(k);
-      for (int q = tid; q < 4 * nt; q += blockDim.x) {
-        const int site = q >> 2, j = q & 3;
+      const int links = 4 * nt;
+      for (int q = tid; q < TPL * links; q += blockDim.x) {
+        int row = 0;
+        if (TPL >= 2 && q >= links) row = 1;
+        if (TPL >= 3 && q >= 2 * links) row = 2;
+        const int link = q - row * links;
+        const int site = link >> 2, j = link & 3;
         const V* src = reinterpret_cast<const V*>(in + (size_t)site * p.a_stride + j * kLinkIn);
-        V* dst = kInPlace ? const_cast<V*>(src) : reinterpret_cast<V*>(out + (size_t)q * kLinkOut);
-        op.apply(src, dst);
+        V* dst = kInPlace ? const_cast<V*>(src) : reinterpret_cast<V*>(out + (size_t)link * kLinkOut);
+        if constexpr (TPL == 1) op.apply(src, dst);
+        else op.apply_row(src, dst, row);
       }
     }
     fence_proxy_async_smem();
@@ -347,7 +356,15 @@ static su3_status run_aos(const Form& f, const LaunchCfg& cfg, const void* a, co
     *ctx.err = "launch configuration needs " + std::to_string(smem) + " B of shared memory (max 232448)";
     return SU3_ERR_INVALID_ARG;
   }
-  auto kern = su3_aos_kernel<Op>;
+  constexpr int kRows = Op::kNeOut / 3;
+  auto kern = su3_aos_kernel<Op, 1>;
+  if (cfg.threads_per_link != 1) {  // 3: one thread per output row
+    if (!Op::kRowSplit || cfg.threads_per_link != 3) {
+      *ctx.err = "threads_per_link must be 1, or 3 (one thread per output row) for the link products";
+      return SU3_ERR_INVALID_ARG;
+    }
+    kern = su3_aos_kernel<Op, (Op::kRowSplit ? kRows : 1)>;
+  }
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(ctx, "cudaFuncSetAttribute", e);
   kern<<<grid, cfg.block, smem, ctx.stream>>>(p);

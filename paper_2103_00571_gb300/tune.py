@@ -1,7 +1,8 @@
 """Autotuner for libsu3's launch configurations.
 
 For each form (dtype x repr x layout) it times su3_mult over a grid of launch configurations
-(block, tile_sites, stages, ctas_per_sm) on a lattice larger than L2, with CUDA events after
+(block, tile_sites, stages, ctas_per_sm and, for AOS, threads per link: one per link or one per
+output row) on a lattice larger than L2, with CUDA events after
 warm-up, and keeps the fastest. The batched kernel's tile/block/stages are tuned the same way on
 the 96-lattice batch. Results go to ``tune_cache.json`` beside this file, keyed by GPU name and SM
 count, and ``apply_cached`` installs them on a handle (bench.py and the tests use the same).
@@ -79,14 +80,15 @@ def candidates(desc):
         return out
     if desc.layout == B.AOS:
         site = B.link_bytes(desc.dtype, desc.repr) * 4
-        out = []
-        for block, tile_bytes, stages, cps in itertools.product((64, 128, 256), (9216, 18432, 36864),
-                                                                (3, 4, 6), (1, 2, 3)):
+        rows = 3 if desc.repr == B.FULL18 else 2  # output rows of the same-repr form
+        out = []  # threads_per_link 3 = one thread per output row
+        for block, tile_bytes, stages, cps, tpl in itertools.product((64, 128, 256), (9216, 18432, 36864),
+                                                                     (3, 4, 6), (1, 2, 3), (1, 3)):
             ts = max(8, tile_bytes // site)
             smem = 1024 + stages * ((ts * site + 127) // 128 * 128)
-            if smem * cps > 227 * 1024:
+            if smem * cps > 227 * 1024 or 4 * ts * (rows if tpl == 3 else 1) < block:
                 continue
-            out.append(dict(block=block, tile_sites=ts, stages=stages, ctas_per_sm=cps))
+            out.append(dict(block=block, tile_sites=ts, stages=stages, ctas_per_sm=cps, threads_per_link=tpl))
         return out
     return [dict(block=bl, tile_sites=lpt, ctas_per_sm=c) for bl in (128, 256) for lpt in (1, 2, 4)
             for c in (2, 4, 8)]
@@ -185,10 +187,11 @@ def time_batched(h, items, reps=10, warm=3):
 def tune_batched(h, log=print):
     items, keep = make_batch96(h)
     best = None
-    for block, ts, stages, cps in itertools.product((64, 128, 256), (16, 32, 64), (2, 3, 4), (1, 2, 3, 4, 6)):
+    for block, ts, stages, cps, tpl in itertools.product((64, 128, 256), (16, 32, 64), (2, 3, 4), (1, 2, 3, 4, 6),
+                                                         (1, 3)):
         if 1024 + stages * ((ts * 576 + 127) // 128 * 128) > 227 * 1024 // cps or block * cps > 1024:
             continue
-        cfg = dict(block=block, tile_sites=ts, stages=stages, ctas_per_sm=cps)
+        cfg = dict(block=block, tile_sites=ts, stages=stages, ctas_per_sm=cps, threads_per_link=tpl)
         h.set_batched_cfg(**cfg)
         ms = time_batched(h, items)
         if best is None or ms < best[0]:

@@ -20,7 +20,7 @@ def test_library_exports_header():
     assert len(names) >= 18
     missing = [n for n in names if not hasattr(L, n)]
     assert not missing, missing
-    assert L.su3_abi_version() == 1
+    assert L.su3_abi_version() == 2
 
 
 def test_header_is_plain_c_and_links(tmp_path):

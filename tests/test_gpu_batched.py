@@ -154,3 +154,30 @@ def test_batched_many_small_lattices(h):
     finally:
         h.set_batched_cfg(**saved)
         torch.cuda.synchronize()
+
+
+def test_batched_row_split_is_bitwise(h):
+    """threads_per_link 3 (one thread per output row) in the batched kernel gives the bits of one
+    thread per link, for FP64, FP32 and FP32-pair lattices, with and without a graph."""
+    saved = h.get_batched_cfg()
+    try:
+        lat = make_batch(h, 24, seed=53, max_extent=10)
+        for k, L in enumerate(lat):
+            if L["dt"] == su3.F64 and k % 4 == 0:
+                L["d"] = su3.Desc(su3.F64, su3.FULL18, su3.AOS, L["V"], 0, su3.F32PAIR)
+                L["item"].desc = L["d"]
+        outs = {}
+        for tpl in (1, 3):
+            h.set_batched_cfg(block=128, tile_sites=16, stages=3, ctas_per_sm=2, threads_per_link=tpl)
+            for use_graph in (False, True):
+                h.mult_batched([L["item"] for L in lat], use_graph=use_graph)
+                h.sync()
+                outs[(tpl, use_graph)] = [unpack(h, L) for L in lat]
+        for key, got in outs.items():
+            for x, y in zip(got, outs[(1, False)]):
+                assert np.array_equal(x, y), key
+        for L, got in zip(lat, outs[(3, True)]):
+            tol = 1e-13 if L["dt"] == su3.F64 else 2e-6
+            assert oracle.error(got, oracle.mult(L["a"], L["b"]))[0] <= tol
+    finally:
+        h.set_batched_cfg(**saved)

@@ -143,19 +143,78 @@ def test_default_launch_cfg_reported_per_arithmetic():
 
 
 def test_launch_cfg_variants_agree():
-    """Every tile size / stage depth / block gives the same bits (sites are independent)."""
+    """Every tile size / stage depth / block / threads per link gives the same bits (sites are
+    independent, and a row computed by its own thread follows the same operation order)."""
     h = su3.Handle(0)  # its own handle: the configurations below stay local to it
     V = 7000
     a, b = gen.lattice(6, V)
     for dt, lay in ((su3.F64, su3.AOS), (su3.F16, su3.AOS), (su3.F32, su3.SOA)):
         base = run_form(h, a, b, dt, layout=lay)
-        cfgs = ({"tile_sites": 7, "stages": 2, "block": 64}, {"tile_sites": 64, "stages": 3, "block": 256},
-                {"tile_sites": 33, "stages": 8, "block": 128, "ctas_per_sm": 1})
+        cfgs = ({"tile_sites": 7, "stages": 2, "block": 64, "threads_per_link": 1},
+                {"tile_sites": 64, "stages": 3, "block": 256},
+                {"tile_sites": 33, "stages": 8, "block": 128, "ctas_per_sm": 1},
+                {"tile_sites": 21, "stages": 3, "block": 256, "threads_per_link": 3},
+                {"tile_sites": 5, "stages": 2, "block": 64, "threads_per_link": 3})
         if lay != su3.AOS:
             cfgs = ({"tile_sites": 1, "block": 64}, {"tile_sites": 2, "block": 256}, {"tile_sites": 4, "ctas_per_sm": 1})
         for cfg in cfgs:
             assert np.array_equal(run_form(h, a, b, dt, layout=lay, cfg=cfg), base), (dt, cfg)
     h.close()
+
+
+@pytest.mark.parametrize("form", [(su3.F64, su3.FULL18, su3.FULL18, su3.F32PAIR, 3),
+                                  (su3.F64, su3.FULL18, su3.FULL18, su3.HYBRID, 3),
+                                  (su3.F64, su3.TWOROW12, su3.TWOROW12, su3.NATIVE, 3),
+                                  (su3.F64, su3.TWOROW12, su3.TWOROW12, su3.F32PAIR, 3),
+                                  (su3.F32, su3.TWOROW12, su3.FULL18, su3.NATIVE, 3),
+                                  (su3.F64, su3.TWOROW12, su3.FULL18, su3.NATIVE, 3)],
+                         ids=["pair", "hybrid", "f64-2row", "pair-2row", "f32-2row-to-full", "f64-2row-to-full"])
+def test_row_split_is_bitwise(form):
+    """One thread per output row (threads_per_link 3; two threads for two-row output) gives the bits
+    of one thread per link, for every op with rows."""
+    h = su3.Handle(0)
+    dt, ri, ro, arith, rows = form
+    V = 3333
+    a, b = gen.lattice(12, V)
+    cfg1 = {"tile_sites": 64, "stages": 3, "block": 256, "threads_per_link": 1}
+    cfgr = {"tile_sites": 24, "stages": 3, "block": 256, "threads_per_link": rows}
+    if arith == su3.HYBRID:
+        cfg1["native_permille"] = cfgr["native_permille"] = 250
+    one = run_form(h, a, b, dt, ri, ro, arith=arith, cfg=cfg1)
+    split = run_form(h, a, b, dt, ri, ro, arith=arith, cfg=cfgr)
+    if arith == su3.HYBRID:  # warps take the native role per tile: each row is one or the other
+        nat = run_form(h, a, b, dt, ri, ro, arith=su3.NATIVE).reshape(-1, 6)
+        pair = run_form(h, a, b, dt, ri, ro, arith=su3.F32PAIR).reshape(-1, 6)
+        s = split.reshape(-1, 6)
+        assert np.all(np.all(s == nat, axis=1) | np.all(s == pair, axis=1))
+    else:
+        assert np.array_equal(one, split)
+    h.close()
+
+
+def test_threads_per_link_validation(h):
+    """threads_per_link must be 1 or 3 (row split); adjacent ops keep one thread per link."""
+    import torch
+    d = su3.Desc(su3.F64, su3.FULL18, su3.AOS, 64)
+    h2 = su3.Handle(0)
+    with pytest.raises(su3.Su3Error):
+        h2.set_launch_cfg(d, threads_per_link=2)
+    with pytest.raises(su3.Su3Error):
+        h2.set_launch_cfg(su3.Desc(su3.F64, su3.FULL18, su3.SOA, 64), threads_per_link=3)
+    with pytest.raises(su3.Su3Error):
+        h2.set_batched_cfg(threads_per_link=2)
+    # a^dagger b and a v on a form whose configuration asks for a row split still run (one thread per link)
+    h2.set_launch_cfg(d, tile_sites=24, stages=3, block=256, threads_per_link=3)
+    V = 64
+    a, b = gen.lattice(13, V)
+    a_dev = to_dev(a)
+    c = torch.empty_like(a_dev)
+    h2.mult_op(su3.OP_AN, d, a_dev, b, d, c)
+    w = torch.empty(V * 24, dtype=torch.float64, device="cuda")
+    h2.mat_vec(d, a_dev, np.linspace(-1, 1, 24), w)
+    h2.sync()
+    assert oracle.error(c.cpu().numpy(), oracle.mult_an(a, b))[0] <= 1e-13
+    h2.close()
 
 
 def test_host_path_matches_device_path(h):
