@@ -314,7 +314,9 @@ def run_native(args, world, rank, local):
     sups = world * V * args.steps / (total_ms * 1e-3)
     clocks = clk.summary()
 
-    # roofline of the dominant kernel (the FP64 AoS kernel is the whole step)
+    # roofline of the dominant kernel (the FP64 AoS kernel is the whole step); its template's
+    # threads per link: 1, or 3 when the launch splits links into rows
+    tpl = 3 if h.get_launch_cfg(d64)["threads_per_link"] == 3 else 1
     fp64_peak = SMS * 2 * 2 * sm_max * 1e6 / 1e12  # 2 DFMA/clk/SM x 2 flop x clock, TFLOP/s
     achieved_tf = FLOP_PER_SITE * V / (per_launch_ms * 1e-3) / 1e12
     achieved_gbs = bytes_per_step / (per_launch_ms * 1e-3) / 1e9
@@ -327,18 +329,20 @@ def run_native(args, world, rank, local):
     if dt != su3.F64:
         tr = traffic_record().get("su3_aos_kernel<%s,full>" % args.dtype, {})
         traffic = tr["bytes_per_site"] * V if tr and tr.get("source_digest") == source_digest() else None
-        roofline = dict(hbm_roof, bound="hbm", traffic=traffic, kernel="su3_aos_kernel<NativeOp<%s,9,3>>" % args.dtype)
+        roofline = dict(hbm_roof, bound="hbm", traffic=traffic,
+                        kernel="su3_aos_kernel<NativeOp<%s,9,3>, %d>" % (args.dtype.upper(), tpl))
     elif args.arith == "native":
         roofline = {"bound": "alu", "achieved": round(achieved_tf, 4), "peak": round(fp64_peak, 4),
                     "unit": "TFLOP/s", "frac": round(achieved_tf / fp64_peak, 4), "traffic": traffic,
-                    "kernel": "su3_aos_kernel<NativeOp<F64,9,3>>",
+                    "kernel": "su3_aos_kernel<NativeOp<F64,9,3>, %d>" % tpl,
                     "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x %.0f MHz (max SM clock)" % sm_max,
                     "hbm": hbm_roof}
     else:
         tr = traffic_record().get("su3_aos_kernel<f64,full,%s>" % args.arith, {})
         traffic = tr["bytes_per_site"] * V if tr and tr.get("source_digest") == source_digest() else None
         roofline = dict(hbm_roof, bound="hbm", traffic=traffic,
-                        kernel="su3_aos_kernel<%s<9,3>>" % ("PairF64Op" if args.arith == "f32pair" else "HybridF64Op"))
+                        kernel="su3_aos_kernel<%s<9,3>, %d>" % ("PairF64Op" if args.arith == "f32pair" else "HybridF64Op",
+                                                                   tpl))
 
     line = {"metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
