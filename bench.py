@@ -350,8 +350,9 @@ def run_native(args, world, rank, local):
             "dtype": ({"native": "f64", "f32pair": "f32x2 (FP64 storage)", "hybrid": "f64 + f32x2"}[args.arith]
                       if dt == su3.F64 else "%s storage, f32 math" % args.dtype),
             "data": "synthetic",
-            "config": {"workload": "L=64 FP64 AoS SU3_Bench link multiply (c[i][j] = a[i][j] x b[j], "
-                                   "%d sites, 576 B read + 576 B written per site)" % V,
+            "config": {"workload": "L=%d %s AoS SU3_Bench link multiply (c[i][j] = a[i][j] x b[j], "
+                                   "%d sites, %d B read + %d B written per site)"
+                                   % (L, args.dtype.upper(), V, bytes_per_step / V / 2, bytes_per_step / V / 2),
                        "lattice": "%d^4" % L,
                        "form": ("f64-full18-aos-" + args.arith) if dt == su3.F64 else args.dtype + "-full18-aos",
                        "seed": SEED,
