@@ -89,6 +89,40 @@ def test_stride_640_keeps_pads_and_canaries(h, arith, cfg):
     assert oracle.error(c[:, :72].reshape(-1), oracle.mult(a, b))[0] <= 1e-13
 
 
+@pytest.mark.parametrize("dtype,stride", [(su3.F64, 592), (su3.F64, 1024), (su3.F32, 304), (su3.F16, 160),
+                                          (su3.BF16, 208)])
+def test_generic_site_strides(h, dtype, stride):
+    """Any 16-byte-multiple site stride at least the link bytes: links land at each site's start,
+    the bytes after them are left alone, for one and three threads per link."""
+    import torch
+    V = 3001
+    a, b = gen.lattice(14, V)
+    d = su3.Desc(dtype, su3.FULL18, su3.AOS, V, stride)
+    dp = su3.Desc(dtype, su3.FULL18, su3.AOS, V)
+    packed = empty_bytes(su3.array_bytes(dp))
+    h.pack(to_dev(a), dp, packed)
+    lb = su3.array_bytes(dp) // V
+    src = torch.full((V * stride,), 0x3C, dtype=torch.uint8, device="cuda")
+    src.view(V, stride)[:, :lb] = packed.view(V, lb)
+    ref = oracle.mult(a, b)
+    tol = {su3.F64: 1e-13, su3.F32: 2e-6, su3.F16: 5e-3, su3.BF16: 3e-2}[dtype]
+    saved = h.get_launch_cfg(d)
+    try:
+        for tpl in (1, 3):
+            h.set_launch_cfg(d, block=128, tile_sites=48, stages=3, ctas_per_sm=2, threads_per_link=tpl)
+            dst = torch.full((V * stride,), 0xC3, dtype=torch.uint8, device="cuda")
+            h.mult(d, src, b, d, dst)
+            h.sync()
+            host = dst.view(V, stride).cpu()
+            assert bool(torch.all(host[:, lb:] == 0xC3)), "bytes after the links were written"
+            out = torch.empty(V * 72, dtype=torch.float64, device="cuda")
+            h.unpack(dp, host[:, :lb].contiguous().view(-1).cuda(), out)
+            h.sync()
+            assert oracle.error(out.cpu().numpy(), ref)[0] <= tol, tpl
+    finally:
+        h.set_launch_cfg(d, **saved)
+
+
 def test_canaries_packed(h):
     import torch
     V = 1237
