@@ -254,7 +254,7 @@ FORMS = [
     ("f64-f32pair-aos", 0, 0, 0, 0, 1), ("f64-f32pair-aosoa32", 0, 0, 0, 1, 1), ("f64-f32pair-2row-aos", 0, 1, 1, 0, 1),
     ("f32-aos", 1, 0, 0, 0), ("f16-aos", 2, 0, 0, 0), ("bf16-aos", 3, 0, 0, 0),
     ("f64-2row-aos", 0, 1, 1, 0), ("f32-2row-aos", 1, 1, 1, 0), ("f16-2row-aos", 2, 1, 1, 0),
-    ("f64-2row-to-full-aos", 0, 1, 0, 0),
+    ("f64-2row-to-full-aos", 0, 1, 0, 0), ("f64-f32pair-2row-to-full-aos", 0, 1, 0, 0, 1),
     ("f64-soa", 0, 0, 0, 2), ("f32-soa", 1, 0, 0, 2), ("f16-soa", 2, 0, 0, 2),
     ("f64-aosoa32", 0, 0, 0, 1), ("f32-aosoa32", 1, 0, 0, 1), ("bf16-aosoa32", 3, 0, 0, 1),
 ]

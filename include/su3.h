@@ -71,8 +71,9 @@ typedef enum { SU3_LAYOUT_AOS = 0, SU3_LAYOUT_AOSOA32 = 1, SU3_LAYOUT_SOA = 2 } 
  * of its FP32 rate, so this is several times faster. Accuracy: about 2^-45 times
  * sum_m |a[k][m]||b[m][l]| per output (measured max 3e-14 against the FP64 oracle on SU(3)
  * data, whose entries are <= 1). Valid for finite inputs with |x| < 2^127; input magnitudes below
- * 2^-74 (including zeros) act as values below 2^-73. Supported reprs: FULL18 -> FULL18 and
- * TWOROW12 -> TWOROW12. Must be NATIVE for F32/F16/BF16 storage (HYBRID, below, likewise).
+ * 2^-74 (including zeros) act as values below 2^-73. All repr pairs are supported; for
+ * TWOROW12 -> FULL18, row 2 of a is rebuilt in FP64 (as NATIVE does) before the FP32-pair product.
+ * Must be NATIVE for F32/F16/BF16 storage (HYBRID, below, likewise).
  * Batched F64 items may use NATIVE or F32PAIR.
  */
 typedef enum { SU3_ARITH_NATIVE = 0, SU3_ARITH_F32PAIR = 1, SU3_ARITH_HYBRID = 2 } su3_arith;

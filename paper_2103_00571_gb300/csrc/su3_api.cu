@@ -142,8 +142,6 @@ su3_status make_form(su3_handle* h, const su3_desc* ad, const su3_desc* cd, Form
     return fail(h, SU3_ERR_INVALID_ARG, "a and c must share dtype, layout, arith and n_sites");
   if (ad->repr == SU3_REPR_FULL18 && cd->repr != SU3_REPR_FULL18)
     return fail(h, SU3_ERR_UNSUPPORTED, "FULL18 input needs FULL18 output");
-  if (ad->arith != SU3_ARITH_NATIVE && ad->repr == SU3_REPR_TWOROW12 && cd->repr == SU3_REPR_FULL18)
-    return fail(h, SU3_ERR_UNSUPPORTED, "F32PAIR arithmetic does not rebuild row 2 (TWOROW12 -> FULL18)");
   f->dtype = ad->dtype;
   f->repr_in = ad->repr;
   f->repr_out = cd->repr;

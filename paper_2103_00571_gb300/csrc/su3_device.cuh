@@ -539,13 +539,31 @@ struct PairF64Op {
       ylb[e] = make_float2(-il, rl);
     }
   }
-  // Output row k: reads input row k and writes output row k (so src and dst may alias).
+  // Output row k: reads input row k and writes output row k (so src and dst may alias). A
+  // two-row input's row 2 is first rebuilt in FP64 from rows 0 and 1 (24 FP64 FMAs, the same
+  // operations as the NATIVE path), then split like any other row.
   __device__ __forceinline__ void apply_row(const V* src, V* dst, int k) const {
-    static_assert(NE_IN == 9 || ROWS_OUT == 2, "F32PAIR rebuilds no row 2");
+    double2 arow[3];
+    if (NE_IN == 6 && ROWS_OUT == 3 && k == 2) {
+      double r0re[3], r0im[3], r1re[3], r1im[3], ore[3], oim[3];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        r0re[m] = src[m].x;
+        r0im[m] = src[m].y;
+        r1re[m] = src[3 + m].x;
+        r1im[m] = src[3 + m].y;
+      }
+      rebuild_row2_elems(r0re, r0im, r1re, r1im, ore, oim);
+#pragma unroll
+      for (int m = 0; m < 3; ++m) arow[m] = make_double2(ore[m], oim[m]);
+    } else {
+#pragma unroll
+      for (int m = 0; m < 3; ++m) arow[m] = src[3 * k + m];
+    }
     float xh[6], xl[6];  // terms 2m: a_re[k][m], 2m+1: a_im[k][m]
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-      const double2 v = src[3 * k + m];
+      const double2 v = arow[m];
       const FF r = split_f64(v.x), i = split_f64(v.y);
       xh[2 * m] = r.h;
       xl[2 * m] = r.l;

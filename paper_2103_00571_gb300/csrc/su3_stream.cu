@@ -429,8 +429,7 @@ su3_status launch_mult(const Form& f, const LaunchCfg& cfg, const void* a, const
       return hyb ? run_layout<HybridF64Op<9, 3>>(f, cfg, a, b, c, ctx) : run_layout<PairF64Op<9, 3>>(f, cfg, a, b, c, ctx);
     if (f.repr_out == SU3_REPR_TWOROW12)
       return hyb ? run_layout<HybridF64Op<6, 2>>(f, cfg, a, b, c, ctx) : run_layout<PairF64Op<6, 2>>(f, cfg, a, b, c, ctx);
-    *ctx.err = "F32PAIR/HYBRID arithmetic does not rebuild row 2 (TWOROW12 -> FULL18)";
-    return SU3_ERR_UNSUPPORTED;
+    return hyb ? run_layout<HybridF64Op<6, 3>>(f, cfg, a, b, c, ctx) : run_layout<PairF64Op<6, 3>>(f, cfg, a, b, c, ctx);
   }
   switch (f.dtype) {
     case SU3_F64: return run_repr<kF64>(f, cfg, a, b, c, ctx);

@@ -201,8 +201,11 @@ def test_launch_cfg_variants_agree():
                                   (su3.F64, su3.TWOROW12, su3.TWOROW12, su3.NATIVE, 3),
                                   (su3.F64, su3.TWOROW12, su3.TWOROW12, su3.F32PAIR, 3),
                                   (su3.F32, su3.TWOROW12, su3.FULL18, su3.NATIVE, 3),
-                                  (su3.F64, su3.TWOROW12, su3.FULL18, su3.NATIVE, 3)],
-                         ids=["pair", "hybrid", "f64-2row", "pair-2row", "f32-2row-to-full", "f64-2row-to-full"])
+                                  (su3.F64, su3.TWOROW12, su3.FULL18, su3.NATIVE, 3),
+                                  (su3.F64, su3.TWOROW12, su3.FULL18, su3.F32PAIR, 3),
+                                  (su3.F64, su3.TWOROW12, su3.FULL18, su3.HYBRID, 3)],
+                         ids=["pair", "hybrid", "f64-2row", "pair-2row", "f32-2row-to-full", "f64-2row-to-full",
+                              "pair-2row-to-full", "hybrid-2row-to-full"])
 def test_row_split_is_bitwise(form):
     """One thread per output row (threads_per_link 3; two threads for two-row output) gives the bits
     of one thread per link, for every op with rows."""

@@ -110,15 +110,18 @@ def test_pack_unpack_roundtrip(h, layout):
 
 
 @pytest.mark.parametrize("layout", LAYOUTS, ids=["aos", "aosoa32", "soa"])
-@pytest.mark.parametrize("rep", [su3.FULL18, su3.TWOROW12], ids=["full", "2row"])
+@pytest.mark.parametrize("reps", [(su3.FULL18, su3.FULL18), (su3.TWOROW12, su3.TWOROW12), (su3.TWOROW12, su3.FULL18)],
+                         ids=["full", "2row", "2row-to-full"])
 @pytest.mark.parametrize("V", SIZES)
-def test_f32pair_vs_oracle(h, layout, rep, V):
-    """FP64 storage with FP32-pair arithmetic: within the FP64 tolerance of the oracle."""
+def test_f32pair_vs_oracle(h, layout, reps, V):
+    """FP64 storage with FP32-pair arithmetic: within the FP64 tolerance of the oracle (two-row to
+    full rebuilds row 2 of a in FP64 first)."""
+    ri, ro = reps
     a, b = gen.lattice(gen.DEFAULT_SEED, V)
     ref = oracle.mult(a, b)
-    got = run_form(h, a, b, su3.F64, rep, rep, layout, arith=su3.F32PAIR)
+    got = run_form(h, a, b, su3.F64, ri, ro, layout, arith=su3.F32PAIR)
     mx, rms = oracle.error(got, ref)
-    assert mx <= tol(su3.F64, rep), (mx, rms)
+    assert mx <= tol(su3.F64, ri, ro), (mx, rms)
 
 
 def test_f32pair_generic_and_constant_inputs(h):
