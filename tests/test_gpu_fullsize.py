@@ -1,5 +1,6 @@
 """The benchmark's own sizes, in the launch configuration bench.py times (tuned or default):
-L=32 and L=48 compared element by element, L=64 on sampled sites the oracle recomputes one by one."""
+L=32, L=48 and the FP64 L=64 step compared element by element over the whole lattice; every
+other L=64 form on sampled sites the oracle recomputes one by one."""
 import numpy as np
 import pytest
 
@@ -83,6 +84,27 @@ def test_L64_sampled(h, dtype, arith, rep, layout):
     ref = oracle.mult_sites(gen.sites_at(gen.DEFAULT_SEED, 0, idx), b)
     mx, rms = oracle.error(got, ref)
     assert mx <= tol(dtype, rep), (mx, rms)
+
+
+@pytest.mark.parametrize("arith", [su3.NATIVE, su3.F32PAIR], ids=["native", "f32pair"])
+def test_L64_f64_aos_full_compare(h, arith):
+    """The bench step itself: the whole L=64 lattice (16,777,216 sites, 1.2 G reals) against the
+    oracle element by element, from a and c in the same device buffers bench.py uses."""
+    import torch
+    V = 64 ** 4
+    a = torch.empty(V * 72, dtype=torch.float64, pin_memory=True)
+    gen.sites(gen.DEFAULT_SEED, 0, V, out=a.numpy())
+    b = gen.bmat(gen.DEFAULT_SEED, 0, V)
+    a_dev = a.cuda()
+    c_dev = torch.empty_like(a_dev)
+    d = su3.Desc(su3.F64, su3.FULL18, su3.AOS, V, 0, arith)
+    h.mult(d, a_dev, b, d, c_dev)
+    h.sync()
+    got = c_dev.cpu().numpy()
+    del a_dev, c_dev
+    ref = oracle.mult(a.numpy(), b)
+    mx, rms = oracle.error(got, ref)
+    assert mx <= 1e-13, (mx, rms)
 
 
 def test_every_bench_form_under_tuned_configs(h):
