@@ -1,7 +1,7 @@
 /*
  * CPU oracle for the SU3_Bench link multiply (arXiv 2103.00571). TEST INFRASTRUCTURE ONLY:
- * the tests, the smoke check and the benchmark's CPU-baseline leg call it; the product path
- * never does. It shares no source with the CUDA library.
+ * the tests, the smoke check, and the benchmark's CPU-baseline leg and reference arm call it; the
+ * product path never does. It shares no source with the CUDA library.
  *
  * Everything is plain FP64 with no contraction into FMA (built with -ffp-contract=off), in the
  * order the definitions state, so that a reader can check it against the paper by eye.
