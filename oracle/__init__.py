@@ -1,7 +1,8 @@
 """CPU FP64 oracle for the SU3_Bench link multiply (arXiv 2103.00571).
 
-TEST INFRASTRUCTURE ONLY. The tests, ``__graft_entry__.smoke()`` and the CPU-baseline leg of
-``bench.py`` may call it; the product library never does, and the two share no code.
+TEST INFRASTRUCTURE ONLY. The tests, ``__graft_entry__.smoke()``, and the CPU-baseline leg and
+reference arm (``--impl reference``) of ``bench.py`` may call it; the product library never does,
+and the two share no code.
 
 The arithmetic lives in ``su3_oracle.c`` (plain C, FP64, no FMA contraction); this module builds
 it with gcc on first use and wraps it with ctypes and numpy. Every function states the passage of
