@@ -68,6 +68,23 @@ def apply_cached(h, key=None):
     return entry
 
 
+def best_layout(dtype, repr_=None, arith=None, key=None):
+    """The internal layout (AOS, AOSOA32 or SOA) with the highest tuned GB/s for this storage type,
+    representation and arithmetic on this GPU, from the tuning cache; None if none was tuned.
+    (Data arrives as AOS, the benchmark's format; pack once into the winner to reuse it.)"""
+    repr_ = B.FULL18 if repr_ is None else repr_
+    arith = B.NATIVE if arith is None else arith
+    if key is None:
+        key = gpu_key()
+    forms = load_cache().get(key, {}).get("forms", {})
+    best = None
+    for name, rec in forms.items():
+        d = parse_form(name)
+        if (d.dtype, d.repr, d.arith) == (dtype, repr_, arith) and (best is None or rec["GBps"] > best[0]):
+            best = (rec["GBps"], d.layout)
+    return None if best is None else best[1]
+
+
 def candidates(desc):
     if desc.arith == B.HYBRID:
         # one or two native warps per CTA; AOS tiles hold at least one link per thread

@@ -48,3 +48,18 @@ def test_reference_arm_line():
     assert line["impl"] == "reference" and line["unit"] == "GB/s" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["kind"] == "oracle"
     assert line["metric"] == bench.METRIC and line["steps"] == 2 and line["higher_is_better"] is True
+
+
+def test_best_layout_from_tuning_cache():
+    """The tuner's layout pick reads the committed cache: for each tuned (dtype, repr, arith) the
+    layout with the highest GB/s, None where nothing was tuned."""
+    from paper_2103_00571_gb300 import tune
+    key = "NVIDIA GB300/152"
+    forms = tune.load_cache()[key]["forms"]
+    for dt in (su3.F64, su3.F32, su3.F16):
+        got = tune.best_layout(dt, su3.FULL18, su3.NATIVE, key=key)
+        rates = {tune.parse_form(n).layout: r["GBps"] for n, r in forms.items()
+                 if (tune.parse_form(n).dtype, tune.parse_form(n).repr, tune.parse_form(n).arith) == (dt, su3.FULL18, su3.NATIVE)}
+        assert got == max(rates, key=rates.get)
+    assert tune.best_layout(su3.F32, su3.TWOROW12, su3.F32PAIR, key=key) is None
+    assert tune.best_layout(su3.F64, key="no such GPU") is None
