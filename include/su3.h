@@ -173,7 +173,9 @@ su3_status su3_mat_vec(su3_handle* h, int32_t adjoint, const su3_desc* a_desc, c
  * and copied back into c_host, with copies and kernels overlapped on the handle's streams.
  * Synchronous: returns when c_host is complete. Pinned host memory (cudaHostRegister or
  * cudaMallocHost) gives full NVLink-C2C speed; pageable memory works but is slower.
- * Allocates (once, then reuses) device staging buffers owned by the handle.
+ * Allocates device staging buffers owned by the handle (three buffers of ~64 MB of input each)
+ * on the first call and whenever a larger site stride needs more; growing them synchronises the
+ * device before freeing the old ones. AOS layout only (chunks are whole sites).
  */
 su3_status su3_mult_host(su3_handle* h, const su3_desc* a_desc, const void* a_host,
                          const double* b, const su3_desc* c_desc, void* c_host, void* stream);
