@@ -13,6 +13,8 @@
 
 #include <string.h>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include <algorithm>
 #include <mutex>
 
@@ -310,8 +312,21 @@ static cudaError_t static_area(int dev, unsigned char** addr, int* sms) {
 
 }  // namespace su3
 
+namespace su3 {
+static su3_status mult_batched_static_impl(int32_t n, const su3_batch_item* items, void* stream);
+}  // namespace su3
+
 extern "C" su3_status su3_mult_batched_static(int32_t n, const su3_batch_item* items, void* stream) {
   using namespace su3;
+  nvtxRangePushA("su3_mult_batched_static");
+  const su3_status s = mult_batched_static_impl(n, items, stream);
+  nvtxRangePop();
+  return s;
+}
+
+namespace su3 {
+
+static su3_status mult_batched_static_impl(int32_t n, const su3_batch_item* items, void* stream) {
   if (n < 0 || (n > 0 && !items)) return SU3_ERR_INVALID_ARG;
   // validate everything and count tiles before touching the GPU
   const BatchCfg cfg = default_batch_cfg();
@@ -386,3 +401,5 @@ extern "C" su3_status su3_mult_batched_static(int32_t n, const su3_batch_item* i
   if (cudaMemcpy(&word, area, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return SU3_ERR_CUDA;
   return word ? SU3_ERR_TIMEOUT : SU3_OK;
 }
+
+}  // namespace su3
