@@ -45,7 +45,22 @@ def parse():
                     help="arithmetic of the FP64 AoS step (native = the plain FP64 method)")
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "f16", "bf16"],
                     help="storage type of the timed step (other than f64: with --quick, for profiling)")
+    ap.add_argument("--launch", default="",
+                    help="launch configuration of the timed step instead of the tuned one, e.g. "
+                         "block=256,tile_sites=64,stages=3,ctas_per_sm=2,threads_per_link=1")
     return ap.parse_args()
+
+
+def parse_launch(text):
+    """'k=v,k=v' -> dict of the su3_launch_cfg fields (ints); raises on unknown keys."""
+    keys = ("block", "tile_sites", "stages", "ctas_per_sm", "native_permille", "threads_per_link")
+    out = {}
+    for item in filter(None, (t.strip() for t in text.split(","))):
+        k, _, v = item.partition("=")
+        if k not in keys:
+            raise SystemExit("--launch: unknown field %r (fields: %s)" % (k, ", ".join(keys)))
+        out[k] = int(v)
+    return out
 
 
 def peaks():
@@ -293,6 +308,8 @@ def run_native(args, world, rank, local):
         a_step = torch.empty(su3.array_bytes(d64), dtype=torch.uint8, device=dev)
         c_step = torch.empty_like(a_step)
         h.pack(a_dev, d64, a_step, stream)
+    if args.launch:
+        h.set_launch_cfg(d64, **parse_launch(args.launch))
     step = lambda: h.mult(d64, a_step, b, d64, c_step, stream)  # noqa: E731
 
     for _ in range(args.warmup):
@@ -359,7 +376,7 @@ def run_native(args, world, rank, local):
                        "inputs": "random SU(3) (Gram-Schmidt on Gaussian rows), one lattice per GPU",
                        "l2": "inputs larger than L2 (%.1f GB touched per step vs 129 MB L2): no flush"
                              % (bytes_per_step / 1e9),
-                       "launch_cfg": h.get_launch_cfg(d64), "tuned": bool(tuned),
+                       "launch_cfg": h.get_launch_cfg(d64), "tuned": bool(tuned) and not args.launch,
                        "parallelism": "replicas" if world > 1 else "single GPU"},
             "site_updates_per_s": round(sups, 1),
             "gflops": round(FLOP_PER_SITE * sups / 1e9, 2),

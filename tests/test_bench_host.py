@@ -63,3 +63,12 @@ def test_best_layout_from_tuning_cache():
         assert got == max(rates, key=rates.get)
     assert tune.best_layout(su3.F32, su3.TWOROW12, su3.F32PAIR, key=key) is None
     assert tune.best_layout(su3.F64, key="no such GPU") is None
+
+
+def test_parse_launch():
+    assert bench.parse_launch("block=256, tile_sites=64,threads_per_link=3") == {
+        "block": 256, "tile_sites": 64, "threads_per_link": 3}
+    assert bench.parse_launch("") == {}
+    import pytest
+    with pytest.raises(SystemExit):
+        bench.parse_launch("warps=8")
