@@ -107,8 +107,13 @@ LaunchCtx ctx_of(su3_handle* h, cudaStream_t st) {
   return c;
 }
 
+// Launch configurations are kept per (dtype, repr, layout, arith, padded): an AOS site stride
+// wider than the links (the paper's 640-byte FP64 site) needs more shared memory per site and
+// gets its own configuration.
 std::tuple<int, int, int, int, int> form_key(const su3_desc* d) {
-  return std::make_tuple((int)d->dtype, (int)d->repr, (int)d->layout, (int)d->arith, 0);
+  const bool padded = d->layout == SU3_LAYOUT_AOS && d->site_stride_bytes != 0 &&
+                      d->site_stride_bytes != 4 * link_bytes(d->dtype, d->repr);
+  return std::make_tuple((int)d->dtype, (int)d->repr, (int)d->layout, (int)d->arith, padded ? 1 : 0);
 }
 
 int64_t resolved_stride(const su3_desc* d) {

@@ -28,19 +28,29 @@ AR = {"native": B.NATIVE, "f32pair": B.F32PAIR, "hybrid": B.HYBRID}
 
 
 def form_name(desc):
+    """dtype-repr-layout-arith, plus -p<stride> for a padded AOS site (e.g. the paper's 640 B)."""
     inv = lambda m, v: [k for k, x in m.items() if x == v][0]  # noqa: E731
-    return "%s-%s-%s-%s" % (inv(DT, desc.dtype), inv(RP, desc.repr), inv(LY, desc.layout), inv(AR, desc.arith))
+    name = "%s-%s-%s-%s" % (inv(DT, desc.dtype), inv(RP, desc.repr), inv(LY, desc.layout), inv(AR, desc.arith))
+    packed = 4 * B.link_bytes(desc.dtype, desc.repr)
+    if desc.layout == B.AOS and desc.site_stride_bytes not in (0, packed):
+        name += "-p%d" % desc.site_stride_bytes
+    return name
 
 
 def parse_form(name, n_sites=0):
-    d, r, l, a = (name.split("-") + ["native"])[:4]
-    return B.Desc(DT[d], RP[r], LY[l], n_sites, 0, AR[a])
+    parts = name.split("-")
+    stride = 0
+    if parts[-1].startswith("p") and parts[-1][1:].isdigit():
+        stride = int(parts.pop()[1:])
+    d, r, l, a = (parts + ["native"])[:4]
+    return B.Desc(DT[d], RP[r], LY[l], n_sites, stride, AR[a])
 
 
 ALL_FORMS = ["f64-full-aos-hybrid", "f64-full-aosoa32-hybrid", "f64-2row-aos-hybrid", "f64-full-aos-f32pair",
              "f64-full-aosoa32-f32pair", "f64-2row-aos-f32pair", "f64-full-aos", "f32-full-aos", "f16-full-aos", "bf16-full-aos", "f64-2row-aos", "f32-2row-aos",
              "f16-2row-aos", "f64-full-soa", "f32-full-soa", "f16-full-soa", "f64-full-aosoa32",
-             "f32-full-aosoa32", "f16-full-aosoa32", "bf16-full-aosoa32"]
+             "f32-full-aosoa32", "f16-full-aosoa32", "bf16-full-aosoa32",
+             "f64-full-aos-native-p640", "f64-full-aos-f32pair-p640"]
 
 
 def gpu_key():
@@ -80,6 +90,8 @@ def best_layout(dtype, repr_=None, arith=None, key=None):
     best = None
     for name, rec in forms.items():
         d = parse_form(name)
+        if d.site_stride_bytes:  # padded AOS sites are a storage format, not a layout choice
+            continue
         if (d.dtype, d.repr, d.arith) == (dtype, repr_, arith) and (best is None or rec["GBps"] > best[0]):
             best = (rec["GBps"], d.layout)
     return None if best is None else best[1]
@@ -96,16 +108,17 @@ def candidates(desc):
             out += [dict(c, native_permille=nw * 1000 // warps) for nw in (1, 2) if nw < warps]
         return out
     if desc.layout == B.AOS:
-        site = B.link_bytes(desc.dtype, desc.repr) * 4
+        site = desc.site_stride_bytes or B.link_bytes(desc.dtype, desc.repr) * 4
         rows = 3 if desc.repr == B.FULL18 else 2  # output rows of the same-repr form
         out = []  # threads_per_link 3 = one thread per output row
-        for block, tile_bytes, stages, cps, tpl in itertools.product((64, 128, 256), (9216, 18432, 36864),
-                                                                     (3, 4, 6), (1, 2, 3), (1, 3)):
-            ts = max(8, tile_bytes // site)
-            smem = 1024 + stages * ((ts * site + 127) // 128 * 128)
-            if smem * cps > 227 * 1024 or 4 * ts * (rows if tpl == 3 else 1) < block:
-                continue
-            out.append(dict(block=block, tile_sites=ts, stages=stages, ctas_per_sm=cps, threads_per_link=tpl))
+        for block, stages, cps, tpl in itertools.product((64, 128, 192, 256), (3, 4, 6), (1, 2, 3), (1, 3)):
+            # tiles of ~9/18/36 KB, and tiles of exactly one or two links per thread
+            sizes = sorted({max(8, tb // site) for tb in (9216, 18432, 36864)} | {block // 4, block // 2})
+            for ts in sizes:
+                smem = 1024 + stages * ((ts * site + 127) // 128 * 128)
+                if smem > 227 * 1024 or (smem + 1024) * cps > 228 * 1024 or 4 * ts * (rows if tpl == 3 else 1) < block:
+                    continue
+                out.append(dict(block=block, tile_sites=ts, stages=stages, ctas_per_sm=cps, threads_per_link=tpl))
         return out
     return [dict(block=bl, tile_sites=lpt, ctas_per_sm=c) for bl in (128, 256) for lpt in (1, 2, 4)
             for c in (2, 4, 8)]

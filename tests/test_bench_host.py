@@ -59,7 +59,8 @@ def test_best_layout_from_tuning_cache():
     for dt in (su3.F64, su3.F32, su3.F16):
         got = tune.best_layout(dt, su3.FULL18, su3.NATIVE, key=key)
         rates = {tune.parse_form(n).layout: r["GBps"] for n, r in forms.items()
-                 if (tune.parse_form(n).dtype, tune.parse_form(n).repr, tune.parse_form(n).arith) == (dt, su3.FULL18, su3.NATIVE)}
+                 if (tune.parse_form(n).dtype, tune.parse_form(n).repr, tune.parse_form(n).arith,
+                     tune.parse_form(n).site_stride_bytes) == (dt, su3.FULL18, su3.NATIVE, 0)}
         assert got == max(rates, key=rates.get)
     assert tune.best_layout(su3.F32, su3.TWOROW12, su3.F32PAIR, key=key) is None
     assert tune.best_layout(su3.F64, key="no such GPU") is None
@@ -72,3 +73,12 @@ def test_parse_launch():
     import pytest
     with pytest.raises(SystemExit):
         bench.parse_launch("warps=8")
+
+
+def test_form_names_round_trip():
+    from paper_2103_00571_gb300 import tune
+    for name in tune.ALL_FORMS:
+        d = tune.parse_form(name)
+        assert tune.parse_form(tune.form_name(d)).key() == d.key()
+    d = tune.parse_form("f64-full-aos-f32pair-p640")
+    assert (d.site_stride_bytes, d.arith) == (640, su3.F32PAIR) and tune.form_name(d) == "f64-full-aos-f32pair-p640"
