@@ -1,0 +1,39 @@
+"""bench.py's JSON line on a GPU: every key of the contract, with values of the right kind."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+pytestmark = pytest.mark.gpu
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def run_bench(*args):
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], capture_output=True, text=True,
+                         check=True, cwd=ROOT, timeout=600)
+    return json.loads(out.stdout.strip().splitlines()[-1])
+
+
+def test_quick_line_has_the_contract_keys():
+    d = run_bench("--quick", "--L", "16", "--steps", "3", "--warmup", "3")
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step", "higher_is_better", "scaling",
+              "vs_baseline", "dtype", "data", "config", "roofline", "gpu_launches", "clocks", "launch_ms"):
+        assert k in d, k
+    assert d["n_gpus"] == 1 and d["steps"] == 3 and d["warmup"] == 3 and d["higher_is_better"] is True
+    assert d["value"] > 0 and d["unit"] == "GB/s" and d["dtype"] == "f64" and d["gpu_launches"] == 3
+    r = d["roofline"]
+    for k in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
+        assert k in r, k
+    assert r["bound"] == "alu" and 0 < r["frac"] < 1.2 and "hbm" in r
+    assert "workload" in d["config"] and d["config"]["lattice"] == "16^4"
+    assert set(d["clocks"]) >= {"sm_mhz", "sm_max_mhz", "reasons"}
+
+
+def test_launch_override_and_reduced_dtype():
+    d = run_bench("--quick", "--L", "16", "--steps", "3", "--warmup", "3", "--dtype", "f16",
+                  "--launch", "block=128,tile_sites=32,stages=3,ctas_per_sm=2,threads_per_link=3")
+    assert d["roofline"]["bound"] == "hbm" and d["config"]["tuned"] is False
+    assert d["config"]["launch_cfg"]["threads_per_link"] == 3 and d["config"]["launch_cfg"]["tile_sites"] == 32
