@@ -122,7 +122,10 @@ typedef struct {
 /* ---- lifetime ---------------------------------------------------------------------------- */
 
 /* Binds a new handle to CUDA device `device` (which becomes current on this thread). The
- * handle owns a small status word in device memory and the batched workspace. */
+ * handle owns a small status word in device memory and the batched workspace. Later calls on the
+ * handle launch on the calling thread's current device, which must be the handle's device; the
+ * pointers and streams passed in must belong to it too. A handle is not thread-safe: use one per
+ * host thread. */
 su3_status su3_init(int device, su3_handle** out);
 
 /* Releases everything the handle owns (after synchronising its device). NULL is a no-op. */
