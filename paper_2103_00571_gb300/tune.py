@@ -7,7 +7,12 @@ warm-up, and keeps the fastest. The batched kernel's tile/block/stages are tuned
 the 96-lattice batch. Results go to ``tune_cache.json`` beside this file, keyed by GPU name and SM
 count, and ``apply_cached`` installs them on a handle (bench.py and the tests use the same).
 
-    python -m paper_2103_00571_gb300.tune [--L 48] [--forms all|f64-aos,...] [--batched]
+    python -m paper_2103_00571_gb300.tune [--L 48] [--forms all|f64-full-aos-f32pair,...] [--batched]
+    python -m paper_2103_00571_gb300.tune --time-batched 5 [--arith f32pair]   # time the batch only
+
+Form names are dtype-repr-layout[-arith][-p<stride>], e.g. f16-2row-aosoa32 or
+f64-full-aos-f32pair-p640 (the paper's padded 640-byte FP64 site). ``best_layout`` ranks the
+tuned layouts of a storage type, and ``apply_cached`` installs the configurations on a handle.
 """
 import argparse
 import itertools
