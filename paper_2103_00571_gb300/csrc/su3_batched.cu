@@ -8,7 +8,8 @@
 // lattice up (a galloping search forward from the previous tile's lattice, since a CTA's tiles
 // come in increasing order) and leaves (lattice, first site, sites) next to the stage, where the
 // computing threads read it after the stage's mbarrier completes. Each tile's link products use
-// that lattice's b (read through the L1 cache; FP32 lattices round it to FP32 once per load).
+// that lattice's b (read through the L1 cache; FP32 lattices round it to FP32 once per load); a
+// thread computes whole links, or single output rows when the launch has threads_per_link 3.
 #include <cuda_runtime.h>
 
 #include <string.h>

@@ -284,7 +284,9 @@ __device__ __forceinline__ void link_mult(const Link<T>& a, const T (&bre)[9], c
 
 // ---- per-link operations used by the streaming kernels ----------------------------------------
 // An op owns this thread's copy of b[j] (j = tid % 4) and turns one input link (NE_IN complex
-// storage elements) into one output link (3*ROWS_OUT elements). `src` and `dst` may alias.
+// storage elements) into one output link (3*ROWS_OUT elements). `src` and `dst` may alias. Ops
+// with kRowSplit also compute a single output row (apply_row), with the same operations as
+// apply(), for launches with one thread per output row.
 
 template <int DT, int NE_IN, int ROWS_OUT>
 struct NativeOp {
@@ -335,7 +337,7 @@ struct NativeOp {
 };
 
 // ---- adjacent SU(3) operations ----------------------------------------------------------------
-// The lattice-QCD building blocks next to the benchmark's a x b: a^dagger x b (MILC's
+// The other per-link SU(3) products of lattice-QCD codes next to the benchmark's a x b: a^dagger x b (MILC's
 // mult_su3_an) and the matrix x colour-vector products a v and a^dagger v (mult_su3_mat_vec and
 // its adjoint), with b or v fixed per link direction exactly as in the SU3_Bench kernel.
 // (a x b^dagger needs no kernel of its own: b^dagger is formed exactly on the host.)

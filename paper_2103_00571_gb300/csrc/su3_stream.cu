@@ -8,11 +8,12 @@
 //
 //  * AOS (the benchmark's Site array): a persistent CTA streams tiles of whole sites through a
 //    `stages`-deep ring of shared-memory buffers. Each tile arrives by one bulk copy completing on
-//    an mbarrier; each thread multiplies links q = tid, tid+block, ... of the tile (link stride in
-//    shared memory 144/96/72/48/36/24 B, all bank-conflict-free or 2-way) and writes the result
-//    back in place; warp 0 then bulk-stores the tile and refills the ring. Site bytes past the four
-//    links (the paper's coordinates, index, parity and pad) are never written: with such a stride
-//    the store is one bulk copy per site.
+//    an mbarrier; each thread multiplies work items q = tid, tid+block, ... of the tile: whole
+//    links, or single output rows when threads_per_link is 3 (link stride in shared memory
+//    144/96/72/48/36/24 B, all bank-conflict-free or 2-way), and writes the result back in place;
+//    warp 0 then bulk-stores the tile and refills the ring. Site bytes past the four links (the
+//    paper's coordinates, index, parity and pad) are never written: with such a stride the store
+//    is one bulk copy per site. A tile too large for the requested CTAs per SM is shrunk.
 //  * SOA / AOSOA32: the element-major layouts are coalesced as they stand, so a thread loads its
 //    links directly with 8/16-byte no-L1-allocate loads and writes with streaming stores.
 #include <cuda_runtime.h>
