@@ -49,3 +49,24 @@ def test_two_rank_max_and_replicas():
         assert p.exitcode == 0
     assert [r[1] for r in res] == [15.0, 15.0]
     assert res[0][2] != res[1][2]  # different replica inputs per rank
+
+
+@pytest.mark.timeout(240)
+def test_reference_arm_under_torchrun_prints_once():
+    """`torchrun --nproc-per-node 2 bench.py --impl reference`: the launch the driver uses for N > 1.
+    Rank 0 alone times the oracle and prints the one JSON line; the other rank exits 0 without
+    work (gloo rendezvous on 127.0.0.1, CPU only)."""
+    import json
+    import subprocess
+    import sys
+    port = _free_port()
+    out = subprocess.run([sys.executable, "-m", "torch.distributed.run", "--nnodes=1", "--nproc-per-node", "2",
+                          "--master-addr", "127.0.0.1", "--master-port", str(port),
+                          os.path.join(ROOT, "bench.py"), "--impl", "reference", "--gpus", "2", "--L", "8",
+                          "--steps", "2", "--warmup", "1"],
+                         capture_output=True, text=True, timeout=200, cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    lines = [l for l in out.stdout.splitlines() if l.startswith("{")]
+    assert len(lines) == 1, out.stdout
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["value"] > 0 and d["n_gpus"] == 2  # the launch's N
