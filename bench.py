@@ -415,8 +415,12 @@ def sample_error(torch, c_dev_f64, ref, V_sample):
 
 
 def forms_leg(h, torch, su3, a_dev, b, V, stream, f64_gbs, ref, V_sample, reps=10):
+    """Every reduced form on the same lattice: site-updates/s, algorithmic GB/s, speedup over the
+    FP64 kernel and error against the oracle; plus the form's pack (FP64 AoS -> form) and unpack
+    (form -> FP64 AoS) throughput, which stay outside the timed step."""
     out = {}
     f64_sups = f64_gbs * 1e9 / 1152.0
+    scratch = torch.empty(V * 72, dtype=torch.float64, device=a_dev.device)  # unpack target
     for name, dt, ri, ro, lay, *ar in FORMS:
         arith = ar[0] if ar else 0
         da = su3.Desc(dt, ri, lay, V, 0, arith)
@@ -432,22 +436,21 @@ def forms_leg(h, torch, su3, a_dev, b, V, stream, f64_gbs, ref, V_sample, reps=1
         h.sync(stream)
         sups = V / (per * 1e-3)
         gbs = su3.site_update_bytes(dt, ri, ro) * sups / 1e9
-        # error on the CPU-baseline sample (first V_sample sites), vs the oracle
-        ds = su3.Desc(dt, ro, lay, V_sample)
-        c64 = torch.empty(V_sample * 72, dtype=torch.float64, device=a_dev.device)
-        if lay == su3.AOS:
-            h.unpack(ds, cbuf, c64, stream)
-        else:  # element-major layouts: unpack the whole lattice, keep the sample
-            full = torch.empty(V * 72, dtype=torch.float64, device=a_dev.device)
-            h.unpack(dc, cbuf, full, stream)
-            c64 = full[: V_sample * 72]
+        # pack and unpack of this form, timed apart from the step (3 launches each)
+        _, pack_ms = time_launches(h, torch, lambda: h.pack(a_dev, da, abuf, stream), 3, stream)
+        _, unpack_ms = time_launches(h, torch, lambda: h.unpack(dc, cbuf, scratch, stream), 3, stream)
         h.sync(stream)
+        # error on the CPU-baseline sample (first V_sample sites), vs the oracle; the last unpack
+        # left the whole lattice in FP64 AoS
+        c64 = scratch[: V_sample * 72]
         err = sample_error(torch, c64, ref, V_sample)
         tol = TOL[(dt, 1 if (ri == 1 and ro == 1) or (ri == 1) else 0)]
         out[name] = {"GBps": round(gbs, 1), "site_updates_per_s": round(sups, 1),
                      "speedup_vs_f64": round(sups / f64_sups, 3), "max_err": err[0], "rms_err": err[1],
-                     "tol": tol, "ok": err[0] <= tol, "ms": round(per, 4), "launch_cfg": h.get_launch_cfg(da)}
-        del abuf, cbuf, c64
+                     "tol": tol, "ok": err[0] <= tol, "ms": round(per, 4), "launch_cfg": h.get_launch_cfg(da),
+                     "pack_GBps": round((576 * V + su3.array_bytes(da)) / (pack_ms * 1e-3) / 1e9, 1),
+                     "unpack_GBps": round((su3.array_bytes(dc) + 576 * V) / (unpack_ms * 1e-3) / 1e9, 1)}
+        del abuf, cbuf
         torch.cuda.empty_cache()
     return out
 

@@ -1,7 +1,9 @@
 // Layout and precision conversion between the benchmark's packed FP64 Site array and the reduced
-// forms (outside the timed path). Pack rounds each real once, to nearest even, straight from FP64
-// (cvt.rn.{f32,f16,bf16}.f64: no FP64 -> FP32 -> FP16 double rounding); unpack widens exactly and
-// rebuilds row 2 of a two-row link as conj(row0 x row1) in FP64.
+// forms (outside the timed path). Unpack stages tiles of 256 links through shared memory, so that
+// the form's side and the FP64 side are each read and written in their own memory order.
+// Pack rounds each real once, to nearest even, straight from FP64 (cvt.rn.{f32,f16,bf16}.f64: no
+// FP64 -> FP32 -> FP16 double rounding); unpack widens exactly and rebuilds row 2 of a two-row
+// link as conj(row0 x row1) in FP64.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -47,55 +49,100 @@ struct Addr {
     if (layout == SU3_LAYOUT_SOA) return ((long long)e * n_links + q) * vec_bytes;
     return (((q >> 5) * ne + e) * 32 + (q & 31)) * (long long)vec_bytes;
   }
+  // Number of work items of a tile of `tl` links (tiles start at multiples of 32 links): tl x ne,
+  // or for AOSOA32 whole blocks of 32 links, whose items past tl the caller skips.
+  __device__ __forceinline__ int items(int tl) const {
+    return (layout == SU3_LAYOUT_AOSOA32 ? (tl + 31) / 32 * 32 : tl) * ne;
+  }
+  // The i-th element of the tile in the form's memory order (so that consecutive threads touch
+  // consecutive addresses): AOS link-major, SOA element-major, AOSOA32 by blocks of 32 links,
+  // element-major inside a block. Returns the tile-relative link (>= tl: skip) and the element.
+  __device__ __forceinline__ void item(int i, int tl, int& ql, int& e) const {
+    if (layout == SU3_LAYOUT_AOS) {
+      ql = i / ne;
+      e = i - ql * ne;
+    } else if (layout == SU3_LAYOUT_SOA) {
+      e = i / tl;
+      ql = i - e * tl;
+    } else {
+      const int blk = i / (32 * ne), rem = i - blk * 32 * ne;
+      e = rem >> 5;
+      ql = blk * 32 + (rem & 31);
+    }
+  }
 };
 
-__global__ void su3_pack_kernel(const double* __restrict__ src, unsigned char* __restrict__ dst, Addr ad,
-                                int dtype) {
-  const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (q >= ad.n_links) return;
-  const double* s = src + q * 18;
-  for (int e = 0; e < ad.ne; ++e) {
-    const double re = s[2 * e], im = s[2 * e + 1];
-    unsigned char* d = dst + ad.off(q, e);
-    if (dtype == SU3_F64) {
-      *reinterpret_cast<double2*>(d) = make_double2(re, im);
-    } else if (dtype == SU3_F32) {
-      *reinterpret_cast<float2*>(d) = make_float2(f64_to_f32_rn(re), f64_to_f32_rn(im));
-    } else if (dtype == SU3_F16) {
-      *reinterpret_cast<unsigned*>(d) = (unsigned)f64_to_f16_rn(re) | ((unsigned)f64_to_f16_rn(im) << 16);
-    } else {
-      *reinterpret_cast<unsigned*>(d) = (unsigned)f64_to_bf16_rn(re) | ((unsigned)f64_to_bf16_rn(im) << 16);
-    }
+constexpr int kPackTile = 256;  // unpack: links per tile, 36 KB of FP64 links in shared memory
+
+__device__ __forceinline__ void store_elem(unsigned char* d, int dtype, double re, double im) {
+  if (dtype == SU3_F64) {
+    *reinterpret_cast<double2*>(d) = make_double2(re, im);
+  } else if (dtype == SU3_F32) {
+    *reinterpret_cast<float2*>(d) = make_float2(f64_to_f32_rn(re), f64_to_f32_rn(im));
+  } else if (dtype == SU3_F16) {
+    *reinterpret_cast<unsigned*>(d) = (unsigned)f64_to_f16_rn(re) | ((unsigned)f64_to_f16_rn(im) << 16);
+  } else {
+    *reinterpret_cast<unsigned*>(d) = (unsigned)f64_to_bf16_rn(re) | ((unsigned)f64_to_bf16_rn(im) << 16);
   }
 }
 
-__global__ void su3_unpack_kernel(const unsigned char* __restrict__ src, double* __restrict__ dst, Addr ad,
-                                  int dtype) {
+__device__ __forceinline__ double2 load_elem(const unsigned char* s, int dtype) {
+  if (dtype == SU3_F64) return *reinterpret_cast<const double2*>(s);
+  if (dtype == SU3_F32) {
+    const float2 v = *reinterpret_cast<const float2*>(s);
+    return make_double2((double)v.x, (double)v.y);
+  }
+  const unsigned w = *reinterpret_cast<const unsigned*>(s);
+  const unsigned short lo = (unsigned short)(w & 0xffffu), hi = (unsigned short)(w >> 16);
+  if (dtype == SU3_F16) return make_double2(f16_to_f64(lo), f16_to_f64(hi));
+  return make_double2(bf16_to_f64(lo), bf16_to_f64(hi));
+}
+
+// FP64 packed AoS links -> the form, one thread per link: its 18 doubles come through the L1
+// cache, each element is rounded and written at the form's address. (A shared-memory staged
+// version, like the unpack below, measured slower for pack on GB300: 4.3 vs 6.3 TB/s for FP64
+// AoSoA32, 3.4 vs 5.7 for two-row FP16, and faster only for FP32/FP16 AoS.)
+__global__ void __launch_bounds__(256) su3_pack_kernel(const double* __restrict__ src, unsigned char* __restrict__ dst,
+                                                       Addr ad, int dtype) {
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= ad.n_links) return;
-  Link<double> l;
-  for (int e = 0; e < ad.ne; ++e) {
-    const unsigned char* s = src + ad.off(q, e);
-    if (dtype == SU3_F64) {
-      double2 v = *reinterpret_cast<const double2*>(s);
-      l.re[e] = v.x;
-      l.im[e] = v.y;
-    } else if (dtype == SU3_F32) {
-      float2 v = *reinterpret_cast<const float2*>(s);
-      l.re[e] = (double)v.x;
-      l.im[e] = (double)v.y;
-    } else {
-      const unsigned w = *reinterpret_cast<const unsigned*>(s);
-      const unsigned short lo = (unsigned short)(w & 0xffffu), hi = (unsigned short)(w >> 16);
-      l.re[e] = dtype == SU3_F16 ? f16_to_f64(lo) : bf16_to_f64(lo);
-      l.im[e] = dtype == SU3_F16 ? f16_to_f64(hi) : bf16_to_f64(hi);
+  const double* s = src + q * 18;
+  for (int e = 0; e < ad.ne; ++e) store_elem(dst + ad.off(q, e), dtype, s[2 * e], s[2 * e + 1]);
+}
+
+// The form -> FP64 packed AoS links: elements come in in the form's memory order, widened
+// exactly into shared memory; two-row links get row 2 = conj(row0 x row1) there; then the FP64
+// links leave with consecutive 16-byte stores.
+__global__ void __launch_bounds__(256) su3_unpack_kernel(const unsigned char* __restrict__ src, double2* __restrict__ dst,
+                                                         Addr ad, int dtype) {
+  __shared__ double2 tile[kPackTile * 9];
+  const long long n_tiles = (ad.n_links + kPackTile - 1) / kPackTile;
+  for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const long long q0 = t * kPackTile;
+    const int tl = (int)min((long long)kPackTile, ad.n_links - q0);
+    for (int i = threadIdx.x; i < ad.items(tl); i += blockDim.x) {
+      int ql, e;
+      ad.item(i, tl, ql, e);
+      if (ql >= tl) continue;
+      tile[ql * 9 + e] = load_elem(src + ad.off(q0 + ql, e), dtype);
     }
-  }
-  if (ad.ne == 6) rebuild_row2(l);
-  double* d = dst + q * 18;
-  for (int e = 0; e < 9; ++e) {
-    d[2 * e] = l.re[e];
-    d[2 * e + 1] = l.im[e];
+    __syncthreads();
+    if (ad.ne == 6) {
+      for (int ql = threadIdx.x; ql < tl; ql += blockDim.x) {
+        double r0re[3], r0im[3], r1re[3], r1im[3], ore[3], oim[3];
+        for (int m = 0; m < 3; ++m) {
+          r0re[m] = tile[ql * 9 + m].x;
+          r0im[m] = tile[ql * 9 + m].y;
+          r1re[m] = tile[ql * 9 + 3 + m].x;
+          r1im[m] = tile[ql * 9 + 3 + m].y;
+        }
+        rebuild_row2_elems(r0re, r0im, r1re, r1im, ore, oim);
+        for (int m = 0; m < 3; ++m) tile[ql * 9 + 6 + m] = make_double2(ore[m], oim[m]);
+      }
+      __syncthreads();
+    }
+    for (int i = threadIdx.x; i < tl * 9; i += blockDim.x) dst[q0 * 9 + i] = tile[i];
+    __syncthreads();
   }
 }
 
@@ -109,12 +156,15 @@ static Addr make_addr(const Form& f) {
   return a;
 }
 
+static int unpack_grid(const Addr& ad, const LaunchCtx& ctx) {
+  const long long n_tiles = (ad.n_links + kPackTile - 1) / kPackTile;
+  return (int)std::max<long long>(1, std::min<long long>(n_tiles, (long long)ctx.num_sms * 6));
+}
+
 su3_status launch_pack(const Form& dst, const double* src, void* dst_dev, const LaunchCtx& ctx) {
   Addr ad = make_addr(dst);
-  const int block = 256;
-  const long long grid = (ad.n_links + block - 1) / block;
-  su3_pack_kernel<<<(unsigned)grid, block, 0, ctx.stream>>>(src, static_cast<unsigned char*>(dst_dev), ad,
-                                                             dst.dtype);
+  const long long grid = (ad.n_links + 255) / 256;
+  su3_pack_kernel<<<(unsigned)grid, 256, 0, ctx.stream>>>(src, static_cast<unsigned char*>(dst_dev), ad, dst.dtype);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     *ctx.err = std::string("su3_pack_kernel launch: ") + cudaGetErrorString(e);
@@ -126,10 +176,8 @@ su3_status launch_pack(const Form& dst, const double* src, void* dst_dev, const 
 
 su3_status launch_unpack(const Form& src, const void* src_dev, double* dst, const LaunchCtx& ctx) {
   Addr ad = make_addr(src);
-  const int block = 256;
-  const long long grid = (ad.n_links + block - 1) / block;
-  su3_unpack_kernel<<<(unsigned)grid, block, 0, ctx.stream>>>(static_cast<const unsigned char*>(src_dev), dst,
-                                                               ad, src.dtype);
+  su3_unpack_kernel<<<unpack_grid(ad, ctx), 256, 0, ctx.stream>>>(static_cast<const unsigned char*>(src_dev),
+                                                                reinterpret_cast<double2*>(dst), ad, src.dtype);
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     *ctx.err = std::string("su3_unpack_kernel launch: ") + cudaGetErrorString(e);
