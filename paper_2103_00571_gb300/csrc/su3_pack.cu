@@ -33,9 +33,6 @@ __device__ __forceinline__ double f16_to_f64(unsigned short h) {
   asm("cvt.f64.f16 %0, %1;" : "=d"(r) : "h"(h));
   return r;
 }
-__device__ __forceinline__ double bf16_to_f64(unsigned short h) {
-  return (double)__uint_as_float((unsigned)h << 16);
-}
 
 // Complex element e of link q in the form's storage: byte offset.
 struct Addr {
@@ -86,16 +83,33 @@ __device__ __forceinline__ void store_elem(unsigned char* d, int dtype, double r
   }
 }
 
+// Exact FP32 -> FP64 widening. Normal numbers and zeros are re-encoded with integer operations
+// (same value, same bits as the hardware conversion, without the FP64 pipe); subnormals,
+// infinities and NaNs (none in SU(3) data) take the hardware conversion.
+__device__ __forceinline__ double widen_f32(float f) {
+  const unsigned b = __float_as_uint(f);
+  const unsigned e8 = (b >> 23) & 0xFFu;
+  if (e8 - 1u < 254u) {
+    const unsigned hi = (b & 0x80000000u) | ((e8 + 896u) << 20) | ((b & 0x7FFFFFu) >> 3);
+    return __hiloint2double((int)hi, (int)(b << 29));
+  }
+  if ((b & 0x7FFFFFFFu) == 0u) return __hiloint2double((int)(b & 0x80000000u), 0);
+  return (double)f;
+}
+
 __device__ __forceinline__ double2 load_elem(const unsigned char* s, int dtype) {
   if (dtype == SU3_F64) return *reinterpret_cast<const double2*>(s);
   if (dtype == SU3_F32) {
     const float2 v = *reinterpret_cast<const float2*>(s);
-    return make_double2((double)v.x, (double)v.y);
+    return make_double2(widen_f32(v.x), widen_f32(v.y));
   }
   const unsigned w = *reinterpret_cast<const unsigned*>(s);
-  const unsigned short lo = (unsigned short)(w & 0xffffu), hi = (unsigned short)(w >> 16);
-  if (dtype == SU3_F16) return make_double2(f16_to_f64(lo), f16_to_f64(hi));
-  return make_double2(bf16_to_f64(lo), bf16_to_f64(hi));
+  if (dtype == SU3_F16) {
+    // binary16 -> binary32 is exact (the half conversion unit), then widened as above
+    const float2 f = __half22float2(*reinterpret_cast<const __half2*>(&w));
+    return make_double2(widen_f32(f.x), widen_f32(f.y));
+  }
+  return make_double2(widen_f32(__uint_as_float(w << 16)), widen_f32(__uint_as_float(w & 0xffff0000u)));
 }
 
 // FP64 packed AoS links -> the form, one thread per link: its 18 doubles come through the L1
