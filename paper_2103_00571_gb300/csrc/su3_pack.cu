@@ -113,15 +113,41 @@ __device__ __forceinline__ double2 load_elem(const unsigned char* s, int dtype) 
 }
 
 // FP64 packed AoS links -> the form, one thread per link: its 18 doubles come through the L1
-// cache, each element is rounded and written at the form's address. (A shared-memory staged
-// version, like the unpack below, measured slower for pack on GB300: 4.3 vs 6.3 TB/s for FP64
-// AoSoA32, 3.4 vs 5.7 for two-row FP16, and faster only for FP32/FP16 AoS.)
+// cache, each element is rounded and written at the form's address. Used for the element-major
+// layouts and two-row AOS, where it measured faster on GB300 than the staged kernel below
+// (6.3 vs 4.3 TB/s for FP64 AoSoA32, 5.7 vs 3.4 for two-row FP16 AOS).
 __global__ void __launch_bounds__(256) su3_pack_kernel(const double* __restrict__ src, unsigned char* __restrict__ dst,
                                                        Addr ad, int dtype) {
   const long long q = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (q >= ad.n_links) return;
   const double* s = src + q * 18;
   for (int e = 0; e < ad.ne; ++e) store_elem(dst + ad.off(q, e), dtype, s[2 * e], s[2 * e + 1]);
+}
+
+constexpr int kPackStageTile = 128;  // staged pack: links per tile, 18 KB of FP64 links
+
+// FP64 packed AoS links -> a FULL18 AOS form, staged: a tile of links comes in with consecutive
+// 16-byte loads into shared memory and leaves element by element in the form's order (for a
+// packed stride, consecutive addresses). Measured faster than the per-link kernel for these
+// forms: FP32 4.96 vs 4.54 TB/s, FP16 4.36 vs 3.73.
+__global__ void __launch_bounds__(256) su3_pack_staged_kernel(const double2* __restrict__ src,
+                                                              unsigned char* __restrict__ dst, Addr ad, int dtype) {
+  __shared__ double2 tile[kPackStageTile * 9];
+  const long long n_tiles = (ad.n_links + kPackStageTile - 1) / kPackStageTile;
+  for (long long t = blockIdx.x; t < n_tiles; t += gridDim.x) {
+    const long long q0 = t * kPackStageTile;
+    const int tl = (int)min((long long)kPackStageTile, ad.n_links - q0);
+    for (int i = threadIdx.x; i < tl * 9; i += blockDim.x) tile[i] = src[q0 * 9 + i];
+    __syncthreads();
+    for (int i = threadIdx.x; i < ad.items(tl); i += blockDim.x) {
+      int ql, e;
+      ad.item(i, tl, ql, e);
+      if (ql >= tl) continue;
+      const double2 v = tile[ql * 9 + e];
+      store_elem(dst + ad.off(q0 + ql, e), dtype, v.x, v.y);
+    }
+    __syncthreads();
+  }
 }
 
 // The form -> FP64 packed AoS links: elements come in in the form's memory order, widened
@@ -177,8 +203,15 @@ static int unpack_grid(const Addr& ad, const LaunchCtx& ctx) {
 
 su3_status launch_pack(const Form& dst, const double* src, void* dst_dev, const LaunchCtx& ctx) {
   Addr ad = make_addr(dst);
-  const long long grid = (ad.n_links + 255) / 256;
-  su3_pack_kernel<<<(unsigned)grid, 256, 0, ctx.stream>>>(src, static_cast<unsigned char*>(dst_dev), ad, dst.dtype);
+  if (ad.layout == SU3_LAYOUT_AOS && ad.ne == 9) {
+    const long long n_tiles = (ad.n_links + kPackStageTile - 1) / kPackStageTile;
+    const int grid = (int)std::max<long long>(1, std::min<long long>(n_tiles, (long long)ctx.num_sms * 8));
+    su3_pack_staged_kernel<<<grid, 256, 0, ctx.stream>>>(reinterpret_cast<const double2*>(src),
+                                                         static_cast<unsigned char*>(dst_dev), ad, dst.dtype);
+  } else {
+    const long long grid = (ad.n_links + 255) / 256;
+    su3_pack_kernel<<<(unsigned)grid, 256, 0, ctx.stream>>>(src, static_cast<unsigned char*>(dst_dev), ad, dst.dtype);
+  }
   cudaError_t e = cudaGetLastError();
   if (e != cudaSuccess) {
     *ctx.err = std::string("su3_pack_kernel launch: ") + cudaGetErrorString(e);
