@@ -11,12 +11,21 @@ batched 96-lattice workload, the end-to-end host-buffer path and the CPU oracle 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--impl native|reference]
 
 Under torchrun (N > 1) every rank runs its own L=64 lattice (replicas: sites are independent, no
-data-path collective; weak scaling); only the timing uses a barrier and a max over ranks.
+data-path collective; weak scaling); only the timing uses a barrier and a max over ranks. With
+--shard the ranks instead split ONE L=64 lattice into contiguous slabs of sites (strong scaling,
+still without a data-path collective).
 """
+import os
+
+# The CPU oracle's OpenMP threads are pinned one per core, packed (set before any library starts
+# an OpenMP runtime); with the default local allocation policy their first touch keeps the
+# oracle's output on the NUMA node of the cores it runs on.
+os.environ.setdefault("OMP_PROC_BIND", "close")
+os.environ.setdefault("OMP_PLACES", "cores")
+
 import argparse
 import ctypes
 import json
-import os
 import statistics
 import subprocess
 import sys
@@ -30,7 +39,6 @@ sys.path.insert(0, ROOT)
 METRIC = "SU(3) link-mult HBM GB/s & site-updates/s at L=64 vs peak; low-prec speedup at error"
 FLOP_PER_SITE = 864  # paper convention: 4 links x 27 complex MACs x (4 mul + 4 add)
 SEED = 2103
-SMS = 152
 
 
 def parse():
@@ -45,6 +53,9 @@ def parse():
                     help="arithmetic of the FP64 AoS step (native = the plain FP64 method)")
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "f16", "bf16"],
                     help="storage type of the timed step (other than f64: with --quick, for profiling)")
+    ap.add_argument("--shard", action="store_true",
+                    help="N > 1: split one lattice into contiguous slabs of sites, one per rank (strong "
+                         "scaling) instead of one lattice per rank (replicas, weak scaling)")
     ap.add_argument("--launch", default="",
                     help="launch configuration of the timed step instead of the tuned one, e.g. "
                          "block=256,tile_sites=64,stages=3,ctas_per_sm=2,threads_per_link=1")
@@ -120,6 +131,15 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+def slab(n_sites, world, rank):
+    """Rank `rank`'s contiguous slab of one lattice split over `world` ranks: (first site, sites).
+    Sizes differ by at most one site (the first n_sites % world ranks take one more), the slabs are
+    disjoint and cover the lattice in rank order; sites are independent, so no rank needs another's
+    data (the paper splits sites equally over threads, §Performance on Xeon)."""
+    base, rem = divmod(n_sites, world)
+    return rank * base + min(rank, rem), base + (1 if rank < rem else 0)
+
+
 def dist_setup(args):
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -151,6 +171,64 @@ def max_over_ranks(x, world, device=None):
 
 # ---- the CPU baseline leg: the oracle, as it stands, on the host cores --------------------------
 
+def _cpulist(text):
+    out = set()
+    for part in filter(None, text.strip().split(",")):
+        lo, _, hi = part.partition("-")
+        out.update(range(int(lo), int(hi or lo) + 1))
+    return out
+
+
+def host_info():
+    """The host the CPU baseline runs on: CPU model, the cores this process may use, the NUMA
+    nodes those cores belong to, and the OpenMP binding of the oracle's threads."""
+    model = None
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        for l in out.splitlines():
+            if l.startswith("Model name:"):
+                model = l.split(":", 1)[1].strip()
+                break
+    except (OSError, subprocess.SubprocessError):
+        pass
+    if not model:
+        try:
+            with open("/proc/cpuinfo") as f:
+                for l in f:
+                    if l.lower().startswith(("model name", "cpu part")):
+                        model = l.split(":", 1)[1].strip()
+                        break
+        except OSError:
+            pass
+    cpus = sorted(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else []
+    nodes = []
+    base = "/sys/devices/system/node"
+    if os.path.isdir(base):
+        for n in sorted(os.listdir(base)):
+            if n.startswith("node") and n[4:].isdigit():
+                try:
+                    with open(os.path.join(base, n, "cpulist")) as f:
+                        if _cpulist(f.read()) & set(cpus):
+                            nodes.append(int(n[4:]))
+                except OSError:
+                    pass
+    return {"cpu_model": model, "cpus_allowed": len(cpus), "numa_nodes_of_cpus": nodes,
+            "omp_proc_bind": os.environ.get("OMP_PROC_BIND"), "omp_places": os.environ.get("OMP_PLACES"),
+            "memory": "first touch by the pinned OpenMP threads under the default local allocation policy, "
+                      "so pages land on the NUMA node(s) of those cores"}
+
+
+def batched_refs(gen, oracle, n=96):
+    """Oracle outputs of every lattice of the 96-lattice batch (part of the CPU-baseline leg: the
+    batched leg's error report compares against them)."""
+    ext = gen.extents(SEED, n)
+    out = []
+    for k in range(n):
+        V = int(np.prod(ext[k]))
+        out.append(oracle.mult(gen.sites(SEED, k, V), gen.bmat(SEED, k, V)))
+    return out
+
+
 def cpu_baseline_leg(a_host, b, V_sample, min_seconds=10.0):
     """Times the FP64 oracle (plain OpenMP loop over sites) on the first V_sample sites of the
     lattice, repeating passes until ~min_seconds of CPU work. Returns (summary, reference c of the
@@ -181,7 +259,9 @@ def cpu_baseline_leg(a_host, b, V_sample, min_seconds=10.0):
     v = np.linspace(-0.5, 0.5, 24)
     extra = {"an": oracle.mult_an(a, b), "na": oracle.mult_na(a, b), "v": v,
              "mv": oracle.mat_vec(a, v), "mv_adj": oracle.mat_vec(a, v, adjoint=True)}
-    summary = {"value": round(gbs, 3), "unit": "GB/s", "cores": cores, "kind": "oracle",
+    import su3_inputs as gen
+    extra["batched"] = batched_refs(gen, oracle)
+    summary = {"value": round(gbs, 3), "unit": "GB/s", "cores": cores, "kind": "oracle", "host": host_info(),
                "one_core_GBps": round(1152.0 * 65536 * n1 / el1 / 1e9, 3),
                "site_updates_per_s": round(V_sample * passes / el, 1),
                "sample": "%d sites (the first %d of the L=64 lattice) x %d passes, %.1f s, FP64, plain C "
@@ -265,7 +345,6 @@ def source_digest():
 
 FORMS = [
     # name, dtype, repr_in, repr_out, layout[, arith]
-    ("f64-hybrid-aos", 0, 0, 0, 0, 2), ("f64-hybrid-aosoa32", 0, 0, 0, 1, 2), ("f64-hybrid-2row-aos", 0, 1, 1, 0, 2),
     ("f64-f32pair-aos", 0, 0, 0, 0, 1), ("f64-f32pair-aosoa32", 0, 0, 0, 1, 1), ("f64-f32pair-2row-aos", 0, 1, 1, 0, 1),
     ("f32-aos", 1, 0, 0, 0), ("f16-aos", 2, 0, 0, 0), ("bf16-aos", 3, 0, 0, 0),
     ("f64-2row-aos", 0, 1, 1, 0), ("f32-2row-aos", 1, 1, 1, 0), ("f16-2row-aos", 2, 1, 1, 0),
@@ -289,13 +368,20 @@ def run_native(args, world, rank, local):
     tuned = tune.apply_cached(h)
     hbm_peak, sm_max, peak_src = peaks()
     L = args.L
-    V = L ** 4
+    V_lattice = L ** 4
+    sms = torch.cuda.get_device_properties(dev).multi_processor_count
+    if args.shard:  # one lattice (id 0), this rank's slab of it
+        first, V = slab(V_lattice, world, rank)
+        lattice_id, sites_all = 0, V_lattice
+    else:  # one lattice per rank
+        first, V = 0, V_lattice
+        lattice_id, sites_all = rank, world * V_lattice
     stream = torch.cuda.current_stream()
 
-    # inputs: this rank's lattice, generated on the host into pinned memory (also the e2e source)
+    # inputs: this rank's sites, generated on the host into pinned memory (also the e2e source)
     a_host = torch.empty(V * 72, dtype=torch.float64, pin_memory=True)
-    gen.sites(SEED, rank, V, out=a_host.numpy())
-    b = gen.bmat(SEED, rank, V)
+    gen.sites(SEED, lattice_id, V_lattice, first_site=first, count=V, out=a_host.numpy())
+    b = gen.bmat(SEED, lattice_id, V_lattice)
     a_dev = a_host.to(dev)
     c_dev = torch.empty_like(a_dev)
     arith = {"native": su3.NATIVE, "f32pair": su3.F32PAIR, "hybrid": su3.HYBRID}[args.arith]
@@ -327,14 +413,14 @@ def run_native(args, world, rank, local):
     launches = h.launch_count() - n_before
     total_ms = max_over_ranks(total_ms, world, dev)
     bytes_per_step = float(su3.site_update_bytes(dt)) * V
-    value = world * bytes_per_step * args.steps / (total_ms * 1e-3) / 1e9
-    sups = world * V * args.steps / (total_ms * 1e-3)
+    value = sites_all * float(su3.site_update_bytes(dt)) * args.steps / (total_ms * 1e-3) / 1e9
+    sups = sites_all * args.steps / (total_ms * 1e-3)
     clocks = clk.summary()
 
     # roofline of the dominant kernel (the FP64 AoS kernel is the whole step); its template's
     # threads per link: 1, or 3 when the launch splits links into rows
     tpl = 3 if h.get_launch_cfg(d64)["threads_per_link"] == 3 else 1
-    fp64_peak = SMS * 2 * 2 * sm_max * 1e6 / 1e12  # 2 DFMA/clk/SM x 2 flop x clock, TFLOP/s
+    fp64_peak = sms * 2 * 2 * sm_max * 1e6 / 1e12  # 2 DFMA/clk/SM x 2 flop x clock, TFLOP/s
     achieved_tf = FLOP_PER_SITE * V / (per_launch_ms * 1e-3) / 1e12
     achieved_gbs = bytes_per_step / (per_launch_ms * 1e-3) / 1e9
     tr = traffic_record().get("su3_aos_kernel<f64,full>", {})
@@ -352,7 +438,8 @@ def run_native(args, world, rank, local):
         roofline = {"bound": "alu", "achieved": round(achieved_tf, 4), "peak": round(fp64_peak, 4),
                     "unit": "TFLOP/s", "frac": round(achieved_tf / fp64_peak, 4), "traffic": traffic,
                     "kernel": "su3_aos_kernel<NativeOp<F64,9,3>, %d>" % tpl,
-                    "peak_source": "FP64 pipe: 152 SMs x 2 DFMA/clk x 2 flop x %.0f MHz (max SM clock)" % sm_max,
+                    "peak_source": "FP64 pipe: %d SMs (this device) x 2 DFMA/clk x 2 flop x %.0f MHz (max SM clock)"
+                                       % (sms, sm_max),
                     "hbm": hbm_roof}
     else:
         tr = traffic_record().get("su3_aos_kernel<f64,full,%s>" % args.arith, {})
@@ -363,13 +450,14 @@ def run_native(args, world, rank, local):
 
     line = {"metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
-            "scaling": "weak", "vs_baseline": None,
+            "scaling": "strong" if args.shard else "weak", "vs_baseline": None,
             "dtype": ({"native": "f64", "f32pair": "f32x2 (FP64 storage)", "hybrid": "f64 + f32x2"}[args.arith]
                       if dt == su3.F64 else "%s storage, f32 math" % args.dtype),
             "data": "synthetic",
             "config": {"workload": "L=%d %s AoS SU3_Bench link multiply (c[i][j] = a[i][j] x b[j], "
-                                   "%d sites, %d B read + %d B written per site)"
-                                   % (L, args.dtype.upper(), V, bytes_per_step / V / 2, bytes_per_step / V / 2),
+                                   "%d sites, %d B read + %d B written per site)%s"
+                                   % (L, args.dtype.upper(), V_lattice, bytes_per_step / V / 2, bytes_per_step / V / 2,
+                                      ", split into %d slabs of contiguous sites" % world if args.shard else ""),
                        "lattice": "%d^4" % L,
                        "form": ("f64-full18-aos-" + args.arith) if dt == su3.F64 else args.dtype + "-full18-aos",
                        "seed": SEED,
@@ -377,7 +465,8 @@ def run_native(args, world, rank, local):
                        "l2": "inputs larger than L2 (%.1f GB touched per step vs 129 MB L2): no flush"
                              % (bytes_per_step / 1e9),
                        "launch_cfg": h.get_launch_cfg(d64), "tuned": bool(tuned) and not args.launch,
-                       "parallelism": "replicas" if world > 1 else "single GPU"},
+                       "parallelism": ("slab shards" if args.shard else "replicas") if world > 1 else "single GPU",
+                       "sms": sms},
             "site_updates_per_s": round(sups, 1),
             "gflops": round(FLOP_PER_SITE * sups / 1e9, 2),
             "roofline": roofline, "gpu_launches": launches, "clocks": clocks,
@@ -398,9 +487,9 @@ def run_native(args, world, rank, local):
                                     "speedup_vs_f64": 1.0, "max_err": fp64_err[0], "rms_err": fp64_err[1],
                                     "tol": 1e-13, "ok": fp64_err[0] <= 1e-13}
     if not args.quick:
-        line["e2e"] = e2e_leg(h, torch, su3, a_host, b, V, args, stream, world, dev, a_dev, c_dev)
+        line["e2e"] = e2e_leg(h, torch, su3, a_host, b, V, args, stream, world, dev, a_dev, c_dev, sites_all)
         if rank == 0:
-            line["batched"] = batched_leg(h, torch, su3, gen)
+            line["batched"] = batched_leg(h, torch, su3, gen, extra["batched"])
     elif rank == 0:
         line["e2e"] = None
     if rank == 0:
@@ -529,7 +618,7 @@ def adjacent_leg(h, torch, su3, a_dev, b, V, stream, extra, V_sample, reps=10):
     return res
 
 
-def e2e_leg(h, torch, su3, a_host, b, V, args, stream, world, dev, a_dev=None, c_dev=None):
+def e2e_leg(h, torch, su3, a_host, b, V, args, stream, world, dev, a_dev=None, c_dev=None, sites_all=None):
     """The same step through the host-buffer entry point: H2D of a from pinned memory, the kernel,
     D2H of c, all inside the timed region (chunked and overlapped inside libsu3). For context, each
     step is followed by the same bytes moved by two plain concurrent copies with no kernel, timed
@@ -556,21 +645,24 @@ def e2e_leg(h, torch, su3, a_host, b, V, args, stream, world, dev, a_dev=None, c
             torch.cuda.synchronize()
             cel += time.perf_counter() - t0
     el = max_over_ranks(el, world, dev)
-    gbs = world * 1152.0 * V * k / el / 1e9
+    sites_all = world * V if sites_all is None else sites_all
+    gbs = 1152.0 * sites_all * k / el / 1e9
     out = {"value": round(gbs, 2), "unit": "GB/s", "h2d_bytes_per_step": 576 * V, "d2h_bytes_per_step": 576 * V,
            "steps": k, "ms_per_step": round(el / k * 1e3, 3),
            "api": "su3_mult_host (pinned host a and c; chunked H2D / kernel / D2H overlapped on 3 streams)"}
     if copies:
         cel = max_over_ranks(cel, world, dev)
-        out["copies_only_GBps"] = round(world * 1152.0 * V * k / cel / 1e9, 2)
+        out["copies_only_GBps"] = round(1152.0 * sites_all * k / cel / 1e9, 2)
         out["vs_copies_only"] = round(gbs / out["copies_only_GBps"], 3)
     del c_host
     return out
 
 
-def batched_leg(h, torch, su3, gen, reps=20):
+def batched_leg(h, torch, su3, gen, refs, reps=20):
     """96 lattices, extents uniform over {4, 6, ..., 24}, FP64 (even) / FP32 (odd): one persistent
-    launch replayed from a CUDA graph vs a loop of per-lattice su3_mult launches."""
+    launch replayed from a CUDA graph vs a loop of per-lattice su3_mult launches. After each
+    variant's timing every lattice's whole output is compared with the oracle's (`refs`): the max
+    error per storage type, against 1e-13 (FP64, native or in FP32 pairs) and 2e-6 (FP32)."""
     ext = gen.extents(SEED, 96)
     items, keep, per = [], [], []
     total_sites = 0
@@ -621,6 +713,18 @@ def batched_leg(h, torch, su3, gen, reps=20):
         e1.synchronize()
         ms = e0.elapsed_time(e1) / reps
         res[name] = {"ms": round(ms, 4), "site_updates_per_s": round(total_sites / (ms * 1e-3), 1)}
+        h.sync(s)
+        errs = {"f64": 0.0, "f32": 0.0}
+        for k, (d, abuf, bk, cbuf) in enumerate(per):
+            o = torch.empty(d.n_sites * 72, dtype=torch.float64, device="cuda")
+            h.unpack(d, cbuf, o, s)
+            h.sync(s)
+            diff = np.abs(o.cpu().numpy() - refs[k])
+            key = "f64" if d.dtype == su3.F64 else "f32"
+            errs[key] = max(errs[key], float(np.nan_to_num(diff, nan=np.inf).max()))
+            cbuf.fill_(0xFF)  # NaN bytes: the next variant must rewrite every output
+        res[name]["max_err"] = errs
+        res[name]["ok"] = errs["f64"] <= 1e-13 and errs["f32"] <= 2e-6
     h.sync(s)
     res["speedup"] = round(res["per_lattice_loop"]["ms"] / res["graph_persistent"]["ms"], 3)
     res["lattices"] = 96

@@ -190,7 +190,9 @@ su3_status su3_mult_host(su3_handle* h, const su3_desc* a_desc, const void* a_ho
  * a CUDA graph keyed by the item list and replayed with cudaGraphLaunch on later identical calls.
  * Supported items: dtype F64 or F32, FULL18, AOS packed; NATIVE arithmetic, or F32PAIR for F64
  * items (b is split into FP32 pairs on the host). The item array is copied at
- * call time into handle-owned device memory (the handle's workspace).
+ * call time into handle-owned device memory (the handle's workspace). Without a graph that
+ * workspace is reused by every call: a call's upload is ordered on the GPU after the previous
+ * call's kernel (an event wait), so calls from one handle may use different streams.
  */
 su3_status su3_mult_batched(su3_handle* h, int32_t n, const su3_batch_item* items, void* stream,
                             int32_t use_graph);
@@ -216,9 +218,11 @@ su3_status su3_mult_batched(su3_handle* h, int32_t n, const su3_batch_item* item
  *  - Synchronous: enqueues the descriptor upload and one kernel on `stream`, waits for `stream`,
  *    and returns SU3_ERR_TIMEOUT if a device-side bounded wait ran out (the status word at the
  *    start of the area, cleared at every call), SU3_ERR_CUDA on a CUDA error.
- *  - Every call on a device shares the one area, which keeps the last call's descriptors: calls
- *    that overlap on the GPU (e.g. from two host threads on different streams) race and must be
- *    serialised by the caller.
+ *  - Every call on a device shares the one area, which keeps the last call's descriptors (the
+ *    status word is cleared at each call). Two calls whose work overlapped on the GPU would race
+ *    on it, so the library runs one call at a time per process: a lock is held from the
+ *    descriptor upload until the call's stream has drained. The descriptors are built in a
+ *    static host table of SU3_STATIC_MAX_LATTICES entries and uploaded with one copy.
  */
 su3_status su3_mult_batched_static(int32_t n, const su3_batch_item* items, void* stream);
 

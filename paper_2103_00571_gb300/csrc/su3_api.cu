@@ -64,8 +64,10 @@ struct su3_handle {
   BatchDesc* bdesc_dev = nullptr;
   BatchDesc* bdesc_host = nullptr;  // pinned
   int bcap = 0;
-  cudaEvent_t bcopy_done = nullptr;
+  cudaEvent_t bcopy_done = nullptr;   // the last upload has read the pinned host table
   bool bcopy_pending = false;
+  cudaEvent_t bkern_done = nullptr;   // the last direct-mode kernel has finished with bdesc_dev
+  bool bkern_pending = false;
   // batched, graph mode (its own descriptor buffers: a replay re-reads them)
   BatchDesc* gdesc_dev = nullptr;
   BatchDesc* gdesc_host = nullptr;
@@ -270,6 +272,7 @@ su3_status su3_finalize(su3_handle* h) {
   cudaFree(h->gdesc_dev);
   cudaFreeHost(h->gdesc_host);
   if (h->bcopy_done) cudaEventDestroy(h->bcopy_done);
+  if (h->bkern_done) cudaEventDestroy(h->bkern_done);
   for (int i = 0; i < kHostBuffers; ++i) {
     cudaFree(h->hbuf_dev[i]);
     if (h->ev_h2d[i]) cudaEventDestroy(h->ev_h2d[i]);
@@ -702,12 +705,27 @@ su3_status su3_mult_batched(su3_handle* h, int32_t n, const su3_batch_item* item
     if (total == 0) return SU3_OK;
     memcpy(h->bdesc_host, tmp.data(), sizeof(BatchDesc) * m);
     if (h->fault & kFaultCopy) return fail(h, SU3_ERR_FAULT_INJECTED, "fault injected at copy");
+    if (!h->bcopy_done) {
+      e = cudaEventCreateWithFlags(&h->bcopy_done, cudaEventDisableTiming);
+      if (e == cudaSuccess) e = cudaEventCreateWithFlags(&h->bkern_done, cudaEventDisableTiming);
+      if (e != cudaSuccess) return cuda_err(h, "cudaEventCreate", e);
+    }
+    // the previous call's kernel may still read bdesc_dev on another stream: the upload that
+    // overwrites it waits for that kernel on the GPU
+    if (h->bkern_pending) {
+      e = cudaStreamWaitEvent(st, h->bkern_done, 0);
+      if (e != cudaSuccess) return cuda_err(h, "cudaStreamWaitEvent", e);
+    }
     e = cudaMemcpyAsync(h->bdesc_dev, h->bdesc_host, sizeof(BatchDesc) * m, cudaMemcpyHostToDevice, st);
     if (e != cudaSuccess) return cuda_err(h, "uploading batch descriptors", e);
-    if (!h->bcopy_done) cudaEventCreateWithFlags(&h->bcopy_done, cudaEventDisableTiming);
     cudaEventRecord(h->bcopy_done, st);
     h->bcopy_pending = true;
-    return launch_batched(h->bdesc_dev, m, total, h->bcfg, ctx_of(h, st));
+    s = launch_batched(h->bdesc_dev, m, total, h->bcfg, ctx_of(h, st));
+    if (s != SU3_OK) return s;
+    e = cudaEventRecord(h->bkern_done, st);
+    if (e != cudaSuccess) return cuda_err(h, "cudaEventRecord", e);
+    h->bkern_pending = true;
+    return SU3_OK;
   }
   // graph mode: key = the raw item list; rebuild the graph when it changes
   std::vector<char> key((const char*)items, (const char*)items + sizeof(su3_batch_item) * n);

@@ -288,9 +288,14 @@ static __device__ __align__(256) unsigned char g_su3_static_area[kStaticBytes];
 
 namespace {
 constexpr int kMaxDevices = 64;
-std::mutex g_static_mu;
+std::mutex g_static_mu;    // guards the per-device addresses below
+std::mutex g_static_call;  // held for a whole call: the host table is reused by the next call
 unsigned char* g_static_addr[kMaxDevices] = {};
 int g_static_sms[kMaxDevices] = {};
+// Host copy of the descriptor table: filled completely, uploaded with one copy, and kept alive
+// (under g_static_call) until the call has waited for its stream, so the copy never reads a
+// source that changes under it, whether or not the driver staged it.
+BatchDesc g_static_host[SU3_STATIC_MAX_LATTICES];
 }  // namespace
 
 // Device address of the static area on the current device (looked up once per device).
@@ -359,17 +364,14 @@ static su3_status mult_batched_static_impl(int32_t n, const su3_batch_item* item
   if (static_area(dev, &area, &sms) != cudaSuccess) return SU3_ERR_CUDA;
   cudaStream_t st = (cudaStream_t)stream;
 
-  // clear the status word, then upload the descriptors in small chunks from a stack buffer (each
-  // pageable-to-device copy has staged its source when it returns, so the buffer can be reused)
-  if (cudaMemsetAsync(area, 0, sizeof(unsigned), st) != cudaSuccess) return SU3_ERR_CUDA;
-  BatchDesc* table = reinterpret_cast<BatchDesc*>(area + kStaticHeader);
-  constexpr int kChunk = 16;
-  BatchDesc buf[kChunk];
-  int filled = 0, written = 0, first_tile = 0;
+  // one call at a time in this process: the host table and the device area are shared
+  std::lock_guard<std::mutex> call_lock(g_static_call);
+  BatchDesc* host = g_static_host;
+  int filled = 0, first_tile = 0;
   for (int i = 0; i < n; ++i) {
     const su3_batch_item& it = items[i];
     if (it.desc.n_sites == 0) continue;
-    BatchDesc& o = buf[filled++];
+    BatchDesc& o = host[filled++];
     o.a = it.a_dev;
     o.c = it.c_dev;
     o.n_sites = it.desc.n_sites;
@@ -380,13 +382,12 @@ static su3_status mult_batched_static_impl(int32_t n, const su3_batch_item* item
     memcpy(o.b, it.b, sizeof(o.b));
     split_b_pairs(&it.b[0][0][0][0], o.bpair);
     first_tile += batch_tile_count(it.desc.n_sites, it.desc.dtype, cfg.tile_sites);
-    if (filled == kChunk || written + filled == m) {
-      if (cudaMemcpyAsync(table + written, buf, sizeof(BatchDesc) * filled, cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return SU3_ERR_CUDA;
-      written += filled;
-      filled = 0;
-    }
   }
+  // clear the status word, then upload the whole table in one copy
+  if (cudaMemsetAsync(area, 0, sizeof(unsigned), st) != cudaSuccess) return SU3_ERR_CUDA;
+  BatchDesc* table = reinterpret_cast<BatchDesc*>(area + kStaticHeader);
+  if (cudaMemcpyAsync(table, host, sizeof(BatchDesc) * filled, cudaMemcpyHostToDevice, st) != cudaSuccess)
+    return SU3_ERR_CUDA;
   std::string err;
   int64_t launches = 0;
   LaunchCtx ctx;
@@ -396,8 +397,10 @@ static su3_status mult_batched_static_impl(int32_t n, const su3_batch_item* item
   ctx.launches = &launches;
   ctx.err = &err;
   su3_status s = launch_batched(table, m, first_tile, cfg, ctx);
+  // wait even when the launch failed: the table copy must be done before the lock is released
+  const cudaError_t se = cudaStreamSynchronize(st);
   if (s != SU3_OK) return s;
-  if (cudaStreamSynchronize(st) != cudaSuccess) return SU3_ERR_CUDA;
+  if (se != cudaSuccess) return SU3_ERR_CUDA;
   unsigned word = 0;
   if (cudaMemcpy(&word, area, sizeof(unsigned), cudaMemcpyDeviceToHost) != cudaSuccess) return SU3_ERR_CUDA;
   return word ? SU3_ERR_TIMEOUT : SU3_OK;

@@ -181,3 +181,33 @@ def test_batched_row_split_is_bitwise(h):
             assert oracle.error(got, oracle.mult(L["a"], L["b"]))[0] <= tol
     finally:
         h.set_batched_cfg(**saved)
+
+
+@pytest.mark.parametrize("f64_arith", ["native", "f32pair"])
+def test_batched_full_bench_mix_vs_oracle(h, f64_arith):
+    """The 96-lattice workload exactly as bench.py times it: extents drawn from {4, 6, ..., 24}
+    with no cap (2,972,320 sites, lattices up to 331,776 sites), even lattices FP64 and odd FP32,
+    one persistent launch replayed from a CUDA graph, the FP64 lattices in plain FP64 or in FP32
+    pairs. Every element of every lattice is compared with the oracle (1e-13 FP64, 2e-6 FP32)."""
+    import torch
+    lat = make_batch(h, 96)
+    assert sum(L["V"] for L in lat) == int(np.prod(gen.extents(2103, 96), axis=1).sum())
+    assert max(L["V"] for L in lat) > 100000  # the large lattices the capped tests never reach
+    if f64_arith == "f32pair":
+        for L in lat:
+            if L["dt"] == su3.F64:
+                L["d"] = su3.Desc(su3.F64, su3.FULL18, su3.AOS, L["V"], 0, su3.F32PAIR)
+                L["item"].desc = L["d"]
+    items = [L["item"] for L in lat]
+    for rep in range(2):  # the capture, then a replay of the same graph
+        for L in lat:
+            L["cbuf"].fill_(0xFF)  # NaN bytes: every output must be rewritten
+        h.mult_batched(items, use_graph=True)
+        h.sync()
+        for L in lat:
+            ref = oracle.mult(L["a"], L["b"])
+            tol = 1e-13 if L["dt"] == su3.F64 else 2e-6
+            err = oracle.error(unpack(h, L), ref)[0]
+            assert err <= tol, (rep, L["V"], L["dt"], err)
+    del lat
+    torch.cuda.empty_cache()

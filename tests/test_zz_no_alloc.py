@@ -3,14 +3,18 @@
 Such callers (plug-ins whose host application owns every device allocation, loops that must not
 stall on cudaMalloc/cudaFree) get an entry point that takes no handle and keeps its descriptor
 table in a statically allocated device area. This test calls it through the C ABI, twice in a
-row, and checks each result against the existing su3_mult_batched entry point. The file is named
-so that pytest collects it last; it also passes on its own in a fresh process.
+row on different inputs, and checks that each result equals, bit for bit, what the existing
+su3_mult_batched entry point produces (both run the same kernel with the same configuration), and
+that every lattice matches the FP64 oracle. The batch holds 40 lattices mixing FP64, FP32 and
+FP64 in FP32-pair arithmetic. The file is named so that pytest collects it last; it also passes on
+its own in a fresh process.
 """
 import ctypes
 
 import numpy as np
 import pytest
 
+import oracle
 import paper_2103_00571_gb300 as su3
 import su3_inputs as gen
 
@@ -25,14 +29,14 @@ def _lattices(h, seed, n):
     out = []
     for k in range(n):
         V = int(np.prod(ext[k]))
-        dt = su3.F64 if k % 2 == 0 else su3.F32
-        d = su3.Desc(dt, su3.FULL18, su3.AOS, V)
-        a64 = torch.from_numpy(gen.sites(seed, k, V)).cuda()
+        kind = k % 3  # 0: FP64 native, 1: FP32, 2: FP64 in FP32 pairs
+        dt = su3.F32 if kind == 1 else su3.F64
+        d = su3.Desc(dt, su3.FULL18, su3.AOS, V, 0, su3.F32PAIR if kind == 2 else su3.NATIVE)
+        a, b = gen.lattice(seed, V, lattice_id=k)
         abuf = torch.empty(su3.array_bytes(d), dtype=torch.uint8, device="cuda")
-        h.pack(a64, d, abuf)
-        b = gen.bmat(seed, k, V)
-        out.append(dict(d=d, V=V, dt=dt, abuf=abuf, b=b,
-                        c_ref=torch.empty_like(abuf), c_new=torch.full_like(abuf, 0x7F)))
+        h.pack(torch.from_numpy(a).cuda(), d, abuf)
+        out.append(dict(d=d, V=V, dt=dt, a=a, abuf=abuf, b=b,
+                        c_ref=torch.full_like(abuf, 0x7F), c_new=torch.full_like(abuf, 0x7F)))
     h.sync()
     return out
 
@@ -56,16 +60,18 @@ def test_static_entry_matches_batched_twice():
     lib = su3.lib()
     stream = torch.cuda.current_stream().cuda_stream
     for call, seed in enumerate((2103, 4242)):  # two calls in a row, different inputs
-        lat = _lattices(h, seed, 24)
+        lat = _lattices(h, seed, 40)
+        assert len(lat) > 16 and any(L["d"].arith == su3.F32PAIR for L in lat)
         h.mult_batched(_items(lat, "c_ref"), use_graph=False)
         h.sync()
         arr = (su3.BatchItem * len(lat))(*_items(lat, "c_new"))
         status = lib.su3_mult_batched_static(len(lat), arr, ctypes.c_void_p(stream))
         assert status == 0, (call, lib.su3_status_string(status))
         for L in lat:
-            ref = _as_f64(h, L, "c_ref")
+            assert torch.equal(L["c_new"], L["c_ref"]), (call, L["V"], L["d"].arith)  # same bytes
             got = _as_f64(h, L, "c_new")
-            assert np.max(np.abs(got - ref)) <= TOL[L["dt"]], (call, L["V"])
+            err = oracle.error(got, oracle.mult(L["a"], L["b"]))[0]
+            assert err <= TOL[L["dt"]], (call, L["V"], err)
     # beyond the stated maximum: rejected before anything runs
     z = lat[0]
     too_many = (su3.BatchItem * 257)(
