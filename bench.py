@@ -22,6 +22,8 @@ import os
 # oracle's output on the NUMA node of the cores it runs on.
 os.environ.setdefault("OMP_PROC_BIND", "close")
 os.environ.setdefault("OMP_PLACES", "cores")
+# the cores this process may use, read before an OpenMP runtime binds the main thread to one core
+CPUS_ALLOWED = sorted(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else []
 
 import argparse
 import ctypes
@@ -200,7 +202,7 @@ def host_info():
                         break
         except OSError:
             pass
-    cpus = sorted(os.sched_getaffinity(0)) if hasattr(os, "sched_getaffinity") else []
+    cpus = CPUS_ALLOWED
     nodes = []
     base = "/sys/devices/system/node"
     if os.path.isdir(base):
