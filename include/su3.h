@@ -96,19 +96,22 @@ typedef struct {
 
 typedef struct su3_handle su3_handle;
 
-/* Launch configuration of the streaming kernels (for the autotuner); 0 fields = default. */
+/* Launch configuration of the streaming kernels (for the autotuner); 0 fields = default.
+ * AOS always streams through shared memory (the staged kernel). AOSOA32 and SOA use the staged
+ * kernel when stages is 2..8 and plain coalesced global loads when stages is 0 (their default). */
 typedef struct {
   int32_t block;        /* threads per CTA: a multiple of 32 in [32, 256] */
-  int32_t tile_sites;   /* AOS: sites per shared-memory tile (1..1024, at most 1 MiB; shrunk at launch
+  int32_t tile_sites;   /* staged: sites per shared-memory tile (1..1024, at most 1 MiB; AOSOA32 a
+                           multiple of 8, SOA at most 64; AOS/AOSOA32 tiles are shrunk at launch
                            until ctas_per_sm CTAs fit in one SM's shared memory);
-                           AOSOA32/SOA: links per thread (1, 2 or 4) */
-  int32_t stages;       /* AOS: shared-memory pipeline depth (2..8) */
+                           AOSOA32/SOA direct loads: links per thread (1, 2 or 4) */
+  int32_t stages;       /* staged: shared-memory pipeline depth (2..8); AOSOA32/SOA: 0 = direct */
   int32_t ctas_per_sm;  /* CTAs per SM in the persistent grid (1..32) */
   int32_t native_permille;  /* HYBRID only: share of each CTA's warps computing natively, 1/1000 */
-  int32_t threads_per_link; /* AOS: 1 = one thread computes a whole link (default); 3 = one thread
-                               per output row (row split: three threads per link, two for TWOROW12
-                               output). su3_mult_op SU3_OP_AN and su3_mat_vec always use 1. Other
-                               layouts: 1. su3_set_batched_cfg: 1 or 3. */
+  int32_t threads_per_link; /* staged: 1 = one thread computes a whole link (default); 3 = one
+                               thread per output row (row split: three threads per link, two for
+                               TWOROW12 output). su3_mult_op SU3_OP_AN and su3_mat_vec always use 1.
+                               Direct loads: 1. su3_set_batched_cfg: 1 or 3. */
 } su3_launch_cfg;
 
 /* One lattice of a batched call. a/c are device pointers; b as in su3_mult. */

@@ -129,17 +129,22 @@ su3_status check_cfg(su3_handle* h, const Form& f, const LaunchCfg& c) {
   if (c.ctas_per_sm < 1 || c.ctas_per_sm > 32) return fail(h, SU3_ERR_INVALID_ARG, "ctas_per_sm must be in [1, 32]");
   if (c.native_permille < 0 || c.native_permille > 1000)
     return fail(h, SU3_ERR_INVALID_ARG, "native_permille must be in [0, 1000]");
-  if (f.layout == SU3_LAYOUT_AOS) {
+  if (f.layout == SU3_LAYOUT_AOS || c.stages != 0) {  // the staged kernel
     if (c.threads_per_link != 1 && c.threads_per_link != 3)
       return fail(h, SU3_ERR_INVALID_ARG, "threads_per_link must be 1 (per link) or 3 (one thread per output row)");
     if (c.stages < 2 || c.stages > 8) return fail(h, SU3_ERR_INVALID_ARG, "stages must be in [2, 8]");
     if (c.tile_sites < 1 || c.tile_sites > 1024) return fail(h, SU3_ERR_INVALID_ARG, "tile_sites must be in [1, 1024]");
-    if ((int64_t)c.tile_sites * f.a_stride > (1 << 20))
+    const int64_t site_bytes = f.layout == SU3_LAYOUT_AOS ? f.a_stride : 4 * link_bytes(f.dtype, f.repr_in);
+    if ((int64_t)c.tile_sites * site_bytes > (1 << 20))
       return fail(h, SU3_ERR_INVALID_ARG, "a tile may not exceed 1 MiB");
-  } else if (c.tile_sites != 1 && c.tile_sites != 2 && c.tile_sites != 4) {
-    return fail(h, SU3_ERR_INVALID_ARG, "links per thread (tile_sites) must be 1, 2 or 4 for SOA/AOSOA32");
+    if (f.layout == SU3_LAYOUT_AOSOA32 && c.tile_sites % 8)
+      return fail(h, SU3_ERR_INVALID_ARG, "AOSOA32 tiles must be a multiple of 8 sites (whole 32-link blocks)");
+    if (f.layout == SU3_LAYOUT_SOA && c.tile_sites > 64)
+      return fail(h, SU3_ERR_INVALID_ARG, "SOA tiles hold at most 64 sites (256 links per element plane)");
+  } else if (c.tile_sites != 1 && c.tile_sites != 2 && c.tile_sites != 4) {  // direct loads
+    return fail(h, SU3_ERR_INVALID_ARG, "links per thread (tile_sites) must be 1, 2 or 4 for SOA/AOSOA32 direct loads");
   } else if (c.threads_per_link != 1) {
-    return fail(h, SU3_ERR_INVALID_ARG, "threads_per_link must be 1 for SOA/AOSOA32");
+    return fail(h, SU3_ERR_INVALID_ARG, "threads_per_link must be 1 for SOA/AOSOA32 direct loads");
   }
   return SU3_OK;
 }

@@ -284,8 +284,10 @@ __device__ __forceinline__ void link_mult(const Link<T>& a, const T (&bre)[9], c
 
 // ---- per-link operations used by the streaming kernels ----------------------------------------
 // An op owns this thread's copy of b[j] (j = tid % 4) and turns one input link (NE_IN complex
-// storage elements) into one output link (3*ROWS_OUT elements). `src` and `dst` may alias. Ops
-// with kRowSplit also compute a single output row (apply_row), with the same operations as
+// storage elements) into one output link (3*ROWS_OUT elements). `src` and `dst` may alias.
+// Element e of the input link is src[e * ES_IN] and of the output link dst[e * ES_OUT]: 1 for a
+// link stored contiguously (AOS), 32 inside an AOSOA32 block, the plane stride inside an SOA tile.
+// Ops with kRowSplit also compute a single output row (apply_row), with the same operations as
 // apply(), for launches with one thread per output row.
 
 template <int DT, int NE_IN, int ROWS_OUT>
@@ -305,34 +307,36 @@ struct NativeOp {
       bim[e] = bj[2 * e + 1];
     }
   }
+  template <int ES_IN = 1, int ES_OUT = 1>
   __device__ __forceinline__ void apply(const V* src, V* dst) const {
     Link<A> la, lc;
 #pragma unroll
-    for (int e = 0; e < NE_IN; ++e) S::unpack(src[e], la.re[e], la.im[e]);
+    for (int e = 0; e < NE_IN; ++e) S::unpack(src[e * ES_IN], la.re[e], la.im[e]);
     if (NE_IN == 6 && ROWS_OUT == 3) rebuild_row2(la);
     link_mult<ROWS_OUT>(la, bre, bim, lc);
 #pragma unroll
-    for (int e = 0; e < 3 * ROWS_OUT; ++e) dst[e] = S::pack(lc.re[e], lc.im[e]);
+    for (int e = 0; e < 3 * ROWS_OUT; ++e) dst[e * ES_OUT] = S::pack(lc.re[e], lc.im[e]);
   }
   // Output row k alone (row split: one thread per output row). Reads input row k only, except
   // that a rebuilt row 2 reads rows 0 and 1; the arithmetic is exactly that of apply().
+  template <int ES_IN = 1, int ES_OUT = 1>
   __device__ __forceinline__ void apply_row(const V* src, V* dst, int k) const {
     A are[3], aim[3], cre[3], cim[3];
     if (NE_IN == 6 && ROWS_OUT == 3 && k == 2) {
       A r0re[3], r0im[3], r1re[3], r1im[3];
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
-        S::unpack(src[m], r0re[m], r0im[m]);
-        S::unpack(src[3 + m], r1re[m], r1im[m]);
+        S::unpack(src[m * ES_IN], r0re[m], r0im[m]);
+        S::unpack(src[(3 + m) * ES_IN], r1re[m], r1im[m]);
       }
       rebuild_row2_elems(r0re, r0im, r1re, r1im, are, aim);
     } else {
 #pragma unroll
-      for (int m = 0; m < 3; ++m) S::unpack(src[3 * k + m], are[m], aim[m]);
+      for (int m = 0; m < 3; ++m) S::unpack(src[(3 * k + m) * ES_IN], are[m], aim[m]);
     }
     row_mult(are, aim, bre, bim, cre, cim);
 #pragma unroll
-    for (int l = 0; l < 3; ++l) dst[3 * k + l] = S::pack(cre[l], cim[l]);
+    for (int l = 0; l < 3; ++l) dst[(3 * k + l) * ES_OUT] = S::pack(cre[l], cim[l]);
   }
 };
 
@@ -359,10 +363,11 @@ struct AnOp {  // c[k][l] = sum_m conj(a[m][k]) b[m][l]
       bim[e] = bj[2 * e + 1];
     }
   }
+  template <int ES_IN = 1, int ES_OUT = 1>
   __device__ __forceinline__ void apply(const V* src, V* dst) const {
     Link<A> la;
 #pragma unroll
-    for (int e = 0; e < 9; ++e) S::unpack(src[e], la.re[e], la.im[e]);
+    for (int e = 0; e < 9; ++e) S::unpack(src[e * ES_IN], la.re[e], la.im[e]);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
 #pragma unroll
@@ -379,7 +384,7 @@ struct AnOp {  // c[k][l] = sum_m conj(a[m][k]) b[m][l]
           im = fma(la.re[3 * m + k], bim[3 * m + l], im);
           im = fma(-la.im[3 * m + k], bre[3 * m + l], im);
         }
-        dst[3 * k + l] = S::pack(re, im);
+        dst[(3 * k + l) * ES_OUT] = S::pack(re, im);
       }
     }
   }
@@ -402,10 +407,11 @@ struct MatVecOp {  // w[k] = sum_m a[k][m] v[m]   (ADJ: sum_m conj(a[m][k]) v[m]
       vim[m] = vj[2 * m + 1];
     }
   }
+  template <int ES_IN = 1, int ES_OUT = 1>
   __device__ __forceinline__ void apply(const V* src, V* dst) const {
     Link<A> la;
 #pragma unroll
-    for (int e = 0; e < 9; ++e) S::unpack(src[e], la.re[e], la.im[e]);
+    for (int e = 0; e < 9; ++e) S::unpack(src[e * ES_IN], la.re[e], la.im[e]);
 #pragma unroll
     for (int k = 0; k < 3; ++k) {
       A re = 0, im = 0;
@@ -418,7 +424,7 @@ struct MatVecOp {  // w[k] = sum_m a[k][m] v[m]   (ADJ: sum_m conj(a[m][k]) v[m]
         im = fma(la.re[e], vim[m], im);
         im = fma(ai, vre[m], im);
       }
-      dst[k] = S::pack(re, im);
+      dst[k * ES_OUT] = S::pack(re, im);
     }
   }
 };
@@ -544,23 +550,24 @@ struct PairF64Op {
   // Output row k: reads input row k and writes output row k (so src and dst may alias). A
   // two-row input's row 2 is first rebuilt in FP64 from rows 0 and 1 (24 FP64 FMAs, the same
   // operations as the NATIVE path), then split like any other row.
+  template <int ES_IN = 1, int ES_OUT = 1>
   __device__ __forceinline__ void apply_row(const V* src, V* dst, int k) const {
     double2 arow[3];
     if (NE_IN == 6 && ROWS_OUT == 3 && k == 2) {
       double r0re[3], r0im[3], r1re[3], r1im[3], ore[3], oim[3];
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
-        r0re[m] = src[m].x;
-        r0im[m] = src[m].y;
-        r1re[m] = src[3 + m].x;
-        r1im[m] = src[3 + m].y;
+        r0re[m] = src[m * ES_IN].x;
+        r0im[m] = src[m * ES_IN].y;
+        r1re[m] = src[(3 + m) * ES_IN].x;
+        r1im[m] = src[(3 + m) * ES_IN].y;
       }
       rebuild_row2_elems(r0re, r0im, r1re, r1im, ore, oim);
 #pragma unroll
       for (int m = 0; m < 3; ++m) arow[m] = make_double2(ore[m], oim[m]);
     } else {
 #pragma unroll
-      for (int m = 0; m < 3; ++m) arow[m] = src[3 * k + m];
+      for (int m = 0; m < 3; ++m) arow[m] = src[(3 * k + m) * ES_IN];
     }
     float xh[6], xl[6];  // terms 2m: a_re[k][m], 2m+1: a_im[k][m]
 #pragma unroll
@@ -582,12 +589,13 @@ struct PairF64Op {
         yh[2 * m + 1] = yb[3 * m + l];
         yl[2 * m + 1] = ylb[3 * m + l];
       }
-      dst[3 * k + l] = dot6_pair2(xh, xl, yh, yl);
+      dst[(3 * k + l) * ES_OUT] = dot6_pair2(xh, xl, yh, yl);
     }
   }
+  template <int ES_IN = 1, int ES_OUT = 1>
   __device__ __forceinline__ void apply(const V* src, V* dst) const {
 #pragma unroll
-    for (int k = 0; k < ROWS_OUT; ++k) apply_row(src, dst, k);
+    for (int k = 0; k < ROWS_OUT; ++k) apply_row<ES_IN, ES_OUT>(src, dst, k);
   }
 };
 
@@ -615,13 +623,15 @@ struct HybridF64Op {
   __device__ __forceinline__ void begin_tile(int k) {
     native = period > 0 && ((k + (int)(threadIdx.x >> 5)) % period) == 0;
   }
+  template <int ES_IN = 1, int ES_OUT = 1>
   __device__ __forceinline__ void apply(const V* src, V* dst) const {
-    if (native) nat.apply(src, dst);
-    else pair.apply(src, dst);
+    if (native) nat.template apply<ES_IN, ES_OUT>(src, dst);
+    else pair.template apply<ES_IN, ES_OUT>(src, dst);
   }
+  template <int ES_IN = 1, int ES_OUT = 1>
   __device__ __forceinline__ void apply_row(const V* src, V* dst, int k) const {
-    if (native) nat.apply_row(src, dst, k);
-    else pair.apply_row(src, dst, k);
+    if (native) nat.template apply_row<ES_IN, ES_OUT>(src, dst, k);
+    else pair.template apply_row<ES_IN, ES_OUT>(src, dst, k);
   }
 };
 

@@ -6,16 +6,21 @@
 // 1-D bulk async copies (the TMA engine), keep b in registers (each thread always serves the same
 // link direction j), and spend the SM only on the 108 FMAs of each link.
 //
-//  * AOS (the benchmark's Site array): a persistent CTA streams tiles of whole sites through a
-//    `stages`-deep ring of shared-memory buffers. Each tile arrives by one bulk copy completing on
-//    an mbarrier; each thread multiplies work items q = tid, tid+block, ... of the tile: whole
-//    links, or single output rows when threads_per_link is 3 (link stride in shared memory
-//    144/96/72/48/36/24 B, all bank-conflict-free or 2-way), and writes the result back in place;
-//    warp 0 then bulk-stores the tile and refills the ring. Site bytes past the four links (the
-//    paper's coordinates, index, parity and pad) are never written: with such a stride the store
-//    is one bulk copy per site. A tile too large for the requested CTAs per SM is shrunk.
-//  * SOA / AOSOA32: the element-major layouts are coalesced as they stand, so a thread loads its
-//    links directly with 8/16-byte no-L1-allocate loads and writes with streaming stores.
+//  * The staged kernel (every layout): a persistent CTA streams tiles of `tile_sites` sites through
+//    a `stages`-deep ring of shared-memory buffers. Each tile arrives by bulk copies completing on
+//    one mbarrier: one copy of whole sites (AOS), one copy of whole 32-link blocks (AOSOA32), or
+//    one copy per element plane into a plane slot of 256 links (SOA). Each thread multiplies work
+//    items q = tid, tid+block, ... of the tile: whole links, or single output rows when
+//    threads_per_link is 3, and writes the result back in place (two-row in, full out: into a
+//    3-deep ring of output buffers in the same layout). Warp 0 then bulk-stores the tile and
+//    refills the ring. Inside a tile a link's elements sit 1 (AOS), 32 (AOSOA32) or 256 (SOA)
+//    storage vectors apart; the element-major layouts put consecutive links in consecutive
+//    vectors, so a warp's shared-memory accesses are conflict-free. AOS site bytes past the four
+//    links (the paper's coordinates, index, parity and pad) are never written: with such a stride
+//    the store is one bulk copy per site. A tile too large for the requested CTAs per SM is shrunk.
+//  * The direct kernel (SOA / AOSOA32 with stages = 0): the element-major layouts are coalesced as
+//    they stand, so a thread loads its links straight from global memory with 8/16-byte
+//    no-L1-allocate loads and writes with streaming stores.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -35,8 +40,9 @@ struct AosArgs {
   const unsigned char* a;
   unsigned char* c;
   long long n_sites;
-  long long a_stride;  // bytes
-  long long c_stride;  // bytes
+  long long a_stride;  // AOS: bytes between sites of a
+  long long c_stride;  // AOS: bytes between sites of c
+  long long n_links;   // SOA: links per element plane in global memory (4 * n_sites)
   int tile_sites;
   int stages;
   int n_tiles;
@@ -47,7 +53,20 @@ struct AosArgs {
   BMat<A> b;
 };
 
-constexpr int kSmemHeader = 1024;  // mbarriers (<= 8 x 8 B) + b (<= 576 B), then 128-aligned data
+constexpr int kSmemHeader = 1024;    // mbarriers (<= 8 x 8 B) + b (<= 576 B), then 128-aligned data
+constexpr int kSoaPlaneLinks = 256;  // links per element plane of an SOA tile in shared memory
+
+// Distance, in storage vectors, between consecutive elements of one link inside a staged tile.
+template <int LAYOUT>
+__host__ __device__ constexpr int tile_elem_stride() {
+  return LAYOUT == SU3_LAYOUT_AOS ? 1 : LAYOUT == SU3_LAYOUT_AOSOA32 ? 32 : kSoaPlaneLinks;
+}
+
+// Element 0 of tile link q (element-major layouts), in storage vectors from the tile start.
+template <int LAYOUT, int NE>
+__device__ __forceinline__ int tile_link_base(int q) {
+  return LAYOUT == SU3_LAYOUT_AOSOA32 ? (q >> 5) * NE * 32 + (q & 31) : q;
+}
 
 // Stages b (72 reals) in shared memory and lets each thread's op take its direction j = tid % 4.
 template <class Op>
@@ -58,20 +77,24 @@ __device__ __forceinline__ void load_b_op(const BMat<typename Op::BArg>& b, type
   op.init(bsh + 18 * (threadIdx.x & 3), native_warps);
 }
 
-// The AOS streaming kernel. Op::kNeIn complex elements per input link (9 full, 6 two-row),
+// The staged streaming kernel. Op::kNeIn complex elements per input link (9 full, 6 two-row),
 // Op::kNeOut per output link. In place (kNeOut == kNeIn): the result overwrites the input tile in
 // shared memory. Otherwise (two-row in, full out) results go to a ring of 3 output buffers.
 // TPL threads per link: 1 (a thread computes whole links), or one thread per output row. The work
 // items of a tile are then ordered row-major over (row, link), so that item q's link direction is
 // still q % 4 = tid % 4 and each thread keeps one b[j] in registers.
-template <class Op, int TPL>
+// Tiles: AOS any number of sites; AOSOA32 a multiple of 8 sites (whole 32-link blocks; the last
+// block of an array is padded, so it is always read whole); SOA at most 64 sites (256 links).
+template <class Op, int TPL, int LAYOUT>
 __global__ void __launch_bounds__(256) su3_aos_kernel(const __grid_constant__ AosArgs<typename Op::BArg> p) {
   using V = typename Op::V;
   using BA = typename Op::BArg;
   constexpr int NE_IN = Op::kNeIn, NE_OUT = Op::kNeOut;
   constexpr bool kInPlace = (NE_OUT == NE_IN);
-  constexpr int kLinkIn = NE_IN * (int)sizeof(V);
-  constexpr int kLinkOut = NE_OUT * (int)sizeof(V);
+  constexpr int kVec = (int)sizeof(V);
+  constexpr int kLinkIn = NE_IN * kVec;
+  constexpr int kLinkOut = NE_OUT * kVec;
+  constexpr int ES = tile_elem_stride<LAYOUT>();
 
   extern __shared__ __align__(128) unsigned char smem[];
   uint64_t* full = reinterpret_cast<uint64_t*>(smem);
@@ -99,10 +122,25 @@ __global__ void __launch_bounds__(256) su3_aos_kernel(const __grid_constant__ Ao
   auto issue_load = [&](int k) {
     const int t = tile_of(k);
     const int s = k % S_;
-    const unsigned bytes = (unsigned)((long long)tile_nsites(t) * p.a_stride);
-    mbar_arrive_expect_tx(&full[s], bytes);
-    bulk_g2s(stage0 + (size_t)s * p.stage_bytes, p.a + (long long)t * p.tile_sites * p.a_stride, bytes,
-             &full[s], pol);
+    const int nt = tile_nsites(t);
+    const long long first = (long long)t * p.tile_sites;
+    unsigned char* dst = stage0 + (size_t)s * p.stage_bytes;
+    if constexpr (LAYOUT == SU3_LAYOUT_AOS) {
+      const unsigned bytes = (unsigned)((long long)nt * p.a_stride);
+      mbar_arrive_expect_tx(&full[s], bytes);
+      bulk_g2s(dst, p.a + first * p.a_stride, bytes, &full[s], pol);
+    } else if constexpr (LAYOUT == SU3_LAYOUT_AOSOA32) {
+      const unsigned bytes = (unsigned)((4 * nt + 31) / 32 * 32 * kLinkIn);
+      mbar_arrive_expect_tx(&full[s], bytes);
+      bulk_g2s(dst, p.a + 4 * first * kLinkIn, bytes, &full[s], pol);
+    } else {
+      const unsigned plane = (unsigned)(4 * nt * kVec);
+      mbar_arrive_expect_tx(&full[s], plane * NE_IN);
+#pragma unroll 1
+      for (int e = 0; e < NE_IN; ++e)
+        bulk_g2s(dst + (size_t)e * kSoaPlaneLinks * kVec, p.a + ((long long)e * p.n_links + 4 * first) * kVec, plane,
+                 &full[s], pol);
+    }
   };
 
   const int prefetch = kInPlace ? S_ - 1 : S_;
@@ -129,11 +167,18 @@ __global__ void __launch_bounds__(256) su3_aos_kernel(const __grid_constant__ Ao
         if (TPL >= 2 && q >= links) row = 1;
         if (TPL >= 3 && q >= 2 * links) row = 2;
         const int link = q - row * links;
-        const int site = link >> 2, j = link & 3;
-        const V* src = reinterpret_cast<const V*>(in + (size_t)site * p.a_stride + j * kLinkIn);
-        V* dst = kInPlace ? const_cast<V*>(src) : reinterpret_cast<V*>(out + (size_t)link * kLinkOut);
-        if constexpr (TPL == 1) op.apply(src, dst);
-        else op.apply_row(src, dst, row);
+        const V* src;
+        V* dst;
+        if constexpr (LAYOUT == SU3_LAYOUT_AOS) {
+          const int site = link >> 2, j = link & 3;
+          src = reinterpret_cast<const V*>(in + (size_t)site * p.a_stride + j * kLinkIn);
+          dst = kInPlace ? const_cast<V*>(src) : reinterpret_cast<V*>(out + (size_t)link * kLinkOut);
+        } else {
+          src = reinterpret_cast<const V*>(in) + tile_link_base<LAYOUT, NE_IN>(link);
+          dst = kInPlace ? const_cast<V*>(src) : reinterpret_cast<V*>(out) + tile_link_base<LAYOUT, NE_OUT>(link);
+        }
+        if constexpr (TPL == 1) op.template apply<ES, ES>(src, dst);
+        else op.template apply_row<ES, ES>(src, dst, row);
       }
     }
     fence_proxy_async_smem();
@@ -145,13 +190,29 @@ __global__ void __launch_bounds__(256) su3_aos_kernel(const __grid_constant__ Ao
     if (tid < 32) {
       // store tile k
       const long long first = (long long)t * p.tile_sites;
-      if (packed_store) {
-        if (tid == 0)
-          bulk_s2g(p.c + first * p.c_stride, out, (unsigned)(nt * 4 * kLinkOut), pol);
+      if constexpr (LAYOUT == SU3_LAYOUT_AOS) {
+        if (packed_store) {
+          if (tid == 0)
+            bulk_s2g(p.c + first * p.c_stride, out, (unsigned)(nt * 4 * kLinkOut), pol);
+        } else {
+          const long long src_stride = kInPlace ? p.a_stride : 4 * kLinkOut;
+          for (int i = tid; i < nt; i += 32)
+            bulk_s2g(p.c + (first + i) * p.c_stride, out + (size_t)i * src_stride, (unsigned)(4 * kLinkOut), pol);
+        }
+      } else if constexpr (LAYOUT == SU3_LAYOUT_AOSOA32) {
+        // whole blocks in one copy; a partial last block (only at the end of the array) one
+        // element row at a time, so that c's padding links are never written
+        const int links = 4 * nt, whole = links / 32, rem = links % 32;
+        unsigned char* cblk = p.c + 4 * first * kLinkOut;
+        if (tid == 0 && whole) bulk_s2g(cblk, out, (unsigned)(whole * 32 * kLinkOut), pol);
+        if (rem && tid < NE_OUT) {
+          const size_t off = ((size_t)whole * NE_OUT * 32 + (size_t)tid * 32) * kVec;
+          bulk_s2g(cblk + off, out + off, (unsigned)(rem * kVec), pol);
+        }
       } else {
-        const long long src_stride = kInPlace ? p.a_stride : 4 * kLinkOut;
-        for (int i = tid; i < nt; i += 32)
-          bulk_s2g(p.c + (first + i) * p.c_stride, out + (size_t)i * src_stride, (unsigned)(4 * kLinkOut), pol);
+        if (tid < NE_OUT)
+          bulk_s2g(p.c + ((long long)tid * p.n_links + 4 * first) * kVec, out + (size_t)tid * kSoaPlaneLinks * kVec,
+                   (unsigned)(4 * nt * kVec), pol);
       }
       bulk_commit();
       if (kInPlace) {
@@ -300,71 +361,90 @@ static su3_status cuda_fail(const LaunchCtx& ctx, const char* what, cudaError_t 
   return SU3_ERR_CUDA;
 }
 
-template <class Op>
+// The staged kernel for one layout. Tile geometry: AOS tile_sites whole sites; AOSOA32 tile_sites
+// a multiple of 8 (whole 32-link blocks); SOA at most 64 sites, each element plane in a slot of
+// 256 links, so an SOA stage is NE x 256 storage vectors whatever tile_sites is.
+template <class Op, int LAYOUT = SU3_LAYOUT_AOS>
 static su3_status run_aos(const Form& f, const LaunchCfg& cfg, const void* a, const double* b, void* c,
                           const LaunchCtx& ctx) {
   using BA = typename Op::BArg;
   using V = typename Op::V;
   constexpr bool kInPlace = (Op::kNeOut == Op::kNeIn);
+  constexpr long long kVec = (long long)sizeof(V);
+  constexpr long long kLinkIn = Op::kNeIn * kVec, kLinkOut = Op::kNeOut * kVec;
+  const long long quantum = LAYOUT == SU3_LAYOUT_AOSOA32 ? 8 : 1;
+  auto r128 = [](long long x) { return (x + 127) / 128 * 128; };
+  auto in_bytes = [&](long long ts) {
+    if (LAYOUT == SU3_LAYOUT_AOS) return r128(ts * f.a_stride);
+    if (LAYOUT == SU3_LAYOUT_AOSOA32) return r128(ts * 4 * kLinkIn);
+    return r128(Op::kNeIn * kSoaPlaneLinks * kVec);
+  };
+  auto out_bytes = [&](long long ts) {
+    if (kInPlace) return 0LL;
+    if (LAYOUT == SU3_LAYOUT_SOA) return r128(Op::kNeOut * kSoaPlaneLinks * kVec);
+    return r128(ts * 4 * kLinkOut);
+  };
+  auto smem_of = [&](long long ts) { return kSmemHeader + cfg.stages * in_bytes(ts) + 3 * out_bytes(ts); };
+
+  long long ts = cfg.tile_sites;
+  if (LAYOUT == SU3_LAYOUT_AOSOA32 && ts % 8) {
+    *ctx.err = "AOSOA32 tiles must be a multiple of 8 sites (whole 32-link blocks)";
+    return SU3_ERR_INVALID_ARG;
+  }
+  if (LAYOUT == SU3_LAYOUT_SOA && ts > kSoaPlaneLinks / 4) {
+    *ctx.err = "SOA tiles hold at most 64 sites (256 links per element plane)";
+    return SU3_ERR_INVALID_ARG;
+  }
+  if (LAYOUT != SU3_LAYOUT_SOA) {
+    // the two-row -> full form shares its configuration with two-row -> two-row but also needs a
+    // 3-deep output ring: shrink the tile until both fit in shared memory
+    if (!kInPlace)
+      while (ts > quantum && smem_of(ts) > 227 * 1024) ts = std::max(quantum, (ts + 1) / 2 / quantum * quantum);
+    // keep ctas_per_sm CTAs resident: a tile shape tuned for the packed stride needs more shared
+    // memory at a padded stride (640 B sites), so shrink the tile (to a multiple of 8 sites) until
+    // that many CTAs fit in one SM's shared memory instead of silently running fewer
+    if (ctx.smem_per_sm > 0) {
+      const long long per_cta = ctx.smem_per_sm / cfg.ctas_per_sm - ctx.smem_reserved;
+      if (smem_of(ts) > per_cta) {
+        while (ts > quantum && smem_of(ts) > per_cta) ts -= quantum;
+        if (ts >= 8) ts &= ~7LL;
+      }
+    }
+  }
   AosArgs<BA> p;
   p.a = static_cast<const unsigned char*>(a);
   p.c = static_cast<unsigned char*>(c);
   p.n_sites = f.n_sites;
   p.a_stride = f.a_stride;
   p.c_stride = f.c_stride;
-  p.tile_sites = cfg.tile_sites;
-  if (!kInPlace) {
-    // the two-row -> full form shares its configuration with two-row -> two-row but also needs a
-    // 3-deep output ring: shrink the tile until both fit in shared memory
-    const long long out_site = 4LL * Op::kNeOut * (long long)sizeof(V);
-    while (p.tile_sites > 1 && kSmemHeader + (long long)cfg.stages * ((p.tile_sites * f.a_stride + 127) / 128 * 128) +
-                                       3 * ((p.tile_sites * out_site + 127) / 128 * 128) > 227 * 1024)
-      p.tile_sites = (p.tile_sites + 1) / 2;
-  }
-  // keep ctas_per_sm CTAs resident: a tile shape tuned for the packed stride needs more shared
-  // memory at a padded stride (640 B sites), so shrink the tile (to a multiple of 8 sites) until
-  // that many CTAs fit in one SM's shared memory instead of silently running fewer
-  if (ctx.smem_per_sm > 0) {
-    const long long out_site = 4LL * Op::kNeOut * (long long)sizeof(V);
-    auto smem_of = [&](long long ts) {
-      return kSmemHeader + (long long)cfg.stages * ((ts * f.a_stride + 127) / 128 * 128) +
-             (kInPlace ? 0 : 3 * ((ts * out_site + 127) / 128 * 128));
-    };
-    const long long per_cta = ctx.smem_per_sm / cfg.ctas_per_sm - ctx.smem_reserved;
-    if (smem_of(p.tile_sites) > per_cta) {
-      long long ts = p.tile_sites;
-      while (ts > 1 && smem_of(ts) > per_cta) --ts;
-      if (ts >= 8) ts &= ~7LL;
-      p.tile_sites = (int)ts;
-    }
-  }
+  p.n_links = 4 * f.n_sites;
+  p.tile_sites = (int)ts;
   p.stages = cfg.stages;
-  const long long n_tiles = (f.n_sites + p.tile_sites - 1) / p.tile_sites;
+  const long long n_tiles = (f.n_sites + ts - 1) / ts;
   if (n_tiles > 0x7fffffffLL) {
     *ctx.err = "too many tiles for one launch: use a larger tile_sites";
     return SU3_ERR_INVALID_ARG;
   }
   p.n_tiles = (int)n_tiles;
-  p.stage_bytes = (unsigned)(((long long)p.tile_sites * f.a_stride + 127) / 128 * 128);
-  p.out_bytes =
-      kInPlace ? 0u : (unsigned)(((long long)p.tile_sites * 4 * Op::kNeOut * sizeof(V) + 127) / 128 * 128);
+  p.stage_bytes = (unsigned)in_bytes(ts);
+  p.out_bytes = (unsigned)out_bytes(ts);
   p.native_warps = native_warps(f, cfg);
   const int grid = (int)std::min<long long>(p.n_tiles, (long long)ctx.num_sms * cfg.ctas_per_sm);
   p.status = ctx.status;
   p.b = make_b<BA>(b);
-  const size_t smem = kSmemHeader + (size_t)p.stages * p.stage_bytes + (kInPlace ? 0 : 3 * (size_t)p.out_bytes);
+  const size_t smem = (size_t)smem_of(ts);
   if (smem > 227 * 1024) {
     *ctx.err = "launch configuration needs " + std::to_string(smem) + " B of shared memory (max 232448)";
     return SU3_ERR_INVALID_ARG;
   }
   constexpr int kRows = Op::kNeOut / 3;
-  auto kern = su3_aos_kernel<Op, 1>;
+  auto kern = su3_aos_kernel<Op, 1, LAYOUT>;
   if (cfg.threads_per_link != 1) {  // 3: one thread per output row
     if (!Op::kRowSplit || cfg.threads_per_link != 3) {
       *ctx.err = "threads_per_link must be 1, or 3 (one thread per output row) for the link products";
       return SU3_ERR_INVALID_ARG;
     }
-    kern = su3_aos_kernel<Op, (Op::kRowSplit ? kRows : 1)>;
+    kern = su3_aos_kernel<Op, (Op::kRowSplit ? kRows : 1), LAYOUT>;
   }
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   if (e != cudaSuccess) return cuda_fail(ctx, "cudaFuncSetAttribute", e);
@@ -406,9 +486,14 @@ template <class Op>
 static su3_status run_layout(const Form& f, const LaunchCfg& cfg, const void* a, const double* b, void* c,
                              const LaunchCtx& ctx) {
   switch (f.layout) {
-    case SU3_LAYOUT_AOS: return run_aos<Op>(f, cfg, a, b, c, ctx);
-    case SU3_LAYOUT_AOSOA32: return run_direct<Op, SU3_LAYOUT_AOSOA32>(f, cfg, a, b, c, ctx);
-    case SU3_LAYOUT_SOA: return run_direct<Op, SU3_LAYOUT_SOA>(f, cfg, a, b, c, ctx);
+    case SU3_LAYOUT_AOS: return run_aos<Op, SU3_LAYOUT_AOS>(f, cfg, a, b, c, ctx);
+    // element-major layouts: staged tiles when the configuration has stages, direct loads otherwise
+    case SU3_LAYOUT_AOSOA32:
+      return cfg.stages ? run_aos<Op, SU3_LAYOUT_AOSOA32>(f, cfg, a, b, c, ctx)
+                        : run_direct<Op, SU3_LAYOUT_AOSOA32>(f, cfg, a, b, c, ctx);
+    case SU3_LAYOUT_SOA:
+      return cfg.stages ? run_aos<Op, SU3_LAYOUT_SOA>(f, cfg, a, b, c, ctx)
+                        : run_direct<Op, SU3_LAYOUT_SOA>(f, cfg, a, b, c, ctx);
   }
   return SU3_ERR_UNSUPPORTED;
 }

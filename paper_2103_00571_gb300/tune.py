@@ -114,9 +114,9 @@ def candidates(desc):
                 continue
             out += [dict(c, native_permille=nw * 1000 // warps) for nw in (1, 2) if nw < warps]
         return out
+    rows = 3 if desc.repr == B.FULL18 else 2  # output rows of the same-repr form
     if desc.layout == B.AOS:
         site = desc.site_stride_bytes or B.link_bytes(desc.dtype, desc.repr) * 4
-        rows = 3 if desc.repr == B.FULL18 else 2  # output rows of the same-repr form
         out = []  # threads_per_link 3 = one thread per output row
         for block, stages, cps, tpl in itertools.product((64, 128, 192, 256), (3, 4, 6), (1, 2, 3), (1, 3)):
             # tiles of ~9/18/36 KB, and tiles of exactly one or two links per thread
@@ -127,8 +127,24 @@ def candidates(desc):
                     continue
                 out.append(dict(block=block, tile_sites=ts, stages=stages, ctas_per_sm=cps, threads_per_link=tpl))
         return out
-    return [dict(block=bl, tile_sites=lpt, ctas_per_sm=c) for bl in (128, 256) for lpt in (1, 2, 4)
-            for c in (2, 4, 8)]
+    # element-major layouts: direct global loads (stages 0: tile_sites = links per thread) ...
+    out = [dict(block=bl, tile_sites=lpt, ctas_per_sm=c) for bl in (128, 256) for lpt in (1, 2, 4)
+           for c in (2, 4, 8)]
+    # ... or the staged kernel (AOSOA32 tiles of whole 32-link blocks; SOA tiles of <= 64 sites in
+    # element planes of 256 links, so an SOA stage is the same size whatever the tile)
+    link = B.link_bytes(desc.dtype, desc.repr)
+    for block, stages, cps, tpl in itertools.product((64, 128, 192, 256), (2, 3, 4, 6), (1, 2, 3, 4), (1, 3)):
+        if desc.layout == B.SOA:
+            sizes = {64, 32}
+        else:
+            sizes = {max(8, tb // (4 * link) // 8 * 8) for tb in (9216, 18432, 36864)} | {max(8, block // 4 // 8 * 8)}
+        for ts in sorted(sizes):
+            stage = link * 4 * (64 if desc.layout == B.SOA else ts)
+            smem = 1024 + stages * ((stage + 127) // 128 * 128)
+            if smem > 227 * 1024 or (smem + 1024) * cps > 228 * 1024 or 4 * ts * (rows if tpl == 3 else 1) < block:
+                continue
+            out.append(dict(block=block, tile_sites=ts, stages=stages, ctas_per_sm=cps, threads_per_link=tpl))
+    return out
 
 
 def time_cfg(h, desc, abuf, b, cbuf, cfg, reps=5, iters=4):
