@@ -72,7 +72,8 @@ typedef enum { SU3_LAYOUT_AOS = 0, SU3_LAYOUT_AOSOA32 = 1, SU3_LAYOUT_SOA = 2 } 
  * sum_m |a[k][m]||b[m][l]| per output (measured max 3e-14 against the FP64 oracle on SU(3)
  * data, whose entries are <= 1). Valid for finite inputs with |x| < 2^127; input magnitudes below
  * 2^-74 (including zeros) act as values below 2^-73. All repr pairs are supported; for
- * TWOROW12 -> FULL18, row 2 of a is rebuilt in FP64 (as NATIVE does) before the FP32-pair product.
+ * TWOROW12 -> FULL18, row 2 of a is rebuilt as conj(row0 x row1) in FP32-pair arithmetic too
+ * (each real a 4-term compensated dot product of the pair splits of rows 0 and 1).
  * Must be NATIVE for F32/F16/BF16 storage (HYBRID, below, likewise).
  * Batched F64 items may use NATIVE or F32PAIR.
  */

@@ -481,13 +481,15 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 
 // The real and imaginary parts of one complex output as two lanes of FP32x2 operations:
-// sum_{t<6} x_t * y_t with x = (xh, xl) broadcast to both lanes and y = (yh, yl) per lane. The
+// sum_{t<N} x_t * y_t with x = (xh, xl) broadcast to both lanes and y = (yh, yl) per lane. The
 // error terms go to three independent accumulators (TwoSum errors, product errors, cross
 // products) so that no dependency chain is longer than two operations per term. The product
 // error x*y - p is one FMA with p negated in its operand (an exact sign flip that costs no
 // instruction; written as a subtraction from zero it cost one extra op per term, 3 % of the time).
-__device__ __forceinline__ double2 dot6_pair2(const float (&xh)[6], const float (&xl)[6], const float2 (&yh)[6],
-                                              const float2 (&yl)[6]) {
+// The result is the unevaluated pair s + L per lane.
+template <int N>
+__device__ __forceinline__ void dot_pair2(const float (&xh)[N], const float (&xl)[N], const float2 (&yh)[N],
+                                          const float2 (&yl)[N], float2& s_out, float2& L_out) {
   const float2 zero = make_float2(0.f, 0.f);
   float2 x0h = make_float2(xh[0], xh[0]), x0l = make_float2(xl[0], xl[0]);
   float2 s = mul2(x0h, yh[0]);
@@ -495,7 +497,7 @@ __device__ __forceinline__ double2 dot6_pair2(const float (&xh)[6], const float 
   float2 Lc = fma2(x0h, yl[0], mul2(x0l, yh[0]));
   float2 Lt = zero;
 #pragma unroll
-  for (int t = 1; t < 6; ++t) {
+  for (int t = 1; t < N; ++t) {
     const float2 xth = make_float2(xh[t], xh[t]), xtl = make_float2(xl[t], xl[t]);
     const float2 p = mul2(xth, yh[t]);
     const float2 s2 = add2(s, p);
@@ -509,8 +511,45 @@ __device__ __forceinline__ double2 dot6_pair2(const float (&xh)[6], const float 
     Lc = fma2(xth, yl[t], Lc);
     Lc = fma2(xtl, yh[t], Lc);
   }
-  const float2 L = add2(add2(Lt, Le), Lc);
+  s_out = s;
+  L_out = add2(add2(Lt, Le), Lc);
+}
+
+// One complex output of the product: the 6-term pair dot product, assembled into FP64.
+__device__ __forceinline__ double2 dot6_pair2(const float (&xh)[6], const float (&xl)[6], const float2 (&yh)[6],
+                                              const float2 (&yl)[6]) {
+  float2 s, L;
+  dot_pair2<6>(xh, xl, yh, yl, s, L);
   return make_double2(f32_bits_to_f64(s.x) + f32_bits_to_f64(L.x), f32_bits_to_f64(s.y) + f32_bits_to_f64(L.y));
+}
+
+// Row 2 of a two-row link, conj(u x v) with u = row 0 and v = row 1, in FP32-pair arithmetic: from
+// the pair splits of the two rows (terms 2m = re, 2m+1 = im of element m) to the pair (wh, wl)
+// of each real of row 2. Element k is conj(u_p v_q - u_q v_p), (p, q) = (k+1, k+2) mod 3; its
+// (re, im) lanes are one 4-term dot product with a's row-0 reals broadcast and row-1 reals,
+// negated or swapped, per lane:
+//   re = up.re vq.re - up.im vq.im - uq.re vp.re + uq.im vp.im
+//   im = -up.re vq.im - up.im vq.re + uq.re vp.im + uq.im vp.re
+// The pair (s, L) of a Dot2 is itself a split of the value (s carries 24 bits, L the rest), so
+// row 2 goes into the product with no FP64 operation.
+__device__ __forceinline__ void rebuild_row2_pair(const float (&uh)[6], const float (&ul)[6], const float (&vh)[6],
+                                                  const float (&vl)[6], float (&wh)[6], float (&wl)[6]) {
+#pragma unroll
+  for (int k = 0; k < 3; ++k) {
+    const int p = (k + 1) % 3, q = (k + 2) % 3;
+    const float xh[4] = {uh[2 * p], uh[2 * p + 1], uh[2 * q], uh[2 * q + 1]};
+    const float xl[4] = {ul[2 * p], ul[2 * p + 1], ul[2 * q], ul[2 * q + 1]};
+    const float2 yh[4] = {make_float2(vh[2 * q], -vh[2 * q + 1]), make_float2(-vh[2 * q + 1], -vh[2 * q]),
+                          make_float2(-vh[2 * p], vh[2 * p + 1]), make_float2(vh[2 * p + 1], vh[2 * p])};
+    const float2 yl[4] = {make_float2(vl[2 * q], -vl[2 * q + 1]), make_float2(-vl[2 * q + 1], -vl[2 * q]),
+                          make_float2(-vl[2 * p], vl[2 * p + 1]), make_float2(vl[2 * p + 1], vl[2 * p])};
+    float2 sv, Lv;
+    dot_pair2<4>(xh, xl, yh, yl, sv, Lv);
+    wh[2 * k] = sv.x;
+    wl[2 * k] = Lv.x;
+    wh[2 * k + 1] = sv.y;
+    wl[2 * k + 1] = Lv.y;
+  }
 }
 
 template <int NE_IN, int ROWS_OUT>
@@ -547,38 +586,22 @@ struct PairF64Op {
       ylb[e] = make_float2(-il, rl);
     }
   }
-  // Output row k: reads input row k and writes output row k (so src and dst may alias). A
-  // two-row input's row 2 is first rebuilt in FP64 from rows 0 and 1 (24 FP64 FMAs, the same
-  // operations as the NATIVE path), then split like any other row.
-  template <int ES_IN = 1, int ES_OUT = 1>
-  __device__ __forceinline__ void apply_row(const V* src, V* dst, int k) const {
-    double2 arow[3];
-    if (NE_IN == 6 && ROWS_OUT == 3 && k == 2) {
-      double r0re[3], r0im[3], r1re[3], r1im[3], ore[3], oim[3];
-#pragma unroll
-      for (int m = 0; m < 3; ++m) {
-        r0re[m] = src[m * ES_IN].x;
-        r0im[m] = src[m * ES_IN].y;
-        r1re[m] = src[(3 + m) * ES_IN].x;
-        r1im[m] = src[(3 + m) * ES_IN].y;
-      }
-      rebuild_row2_elems(r0re, r0im, r1re, r1im, ore, oim);
-#pragma unroll
-      for (int m = 0; m < 3; ++m) arow[m] = make_double2(ore[m], oim[m]);
-    } else {
-#pragma unroll
-      for (int m = 0; m < 3; ++m) arow[m] = src[(3 * k + m) * ES_IN];
-    }
-    float xh[6], xl[6];  // terms 2m: a_re[k][m], 2m+1: a_im[k][m]
+  // The pair split of input row r (terms 2m: re, 2m+1: im of element m).
+  template <int ES_IN>
+  __device__ __forceinline__ void split_row(const V* src, int r, float (&xh)[6], float (&xl)[6]) const {
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
-      const double2 v = arow[m];
-      const FF r = split_f64(v.x), i = split_f64(v.y);
-      xh[2 * m] = r.h;
-      xl[2 * m] = r.l;
-      xh[2 * m + 1] = i.h;
-      xl[2 * m + 1] = i.l;
+      const double2 v = src[(3 * r + m) * ES_IN];
+      const FF re = split_f64(v.x), im = split_f64(v.y);
+      xh[2 * m] = re.h;
+      xl[2 * m] = re.l;
+      xh[2 * m + 1] = im.h;
+      xl[2 * m + 1] = im.l;
     }
+  }
+  // Output row k from the pair split (xh, xl) of the input row.
+  template <int ES_OUT>
+  __device__ __forceinline__ void row_out(const float (&xh)[6], const float (&xl)[6], V* dst, int k) const {
 #pragma unroll
     for (int l = 0; l < 3; ++l) {
       float2 yh[6], yl[6];
@@ -592,10 +615,37 @@ struct PairF64Op {
       dst[(3 * k + l) * ES_OUT] = dot6_pair2(xh, xl, yh, yl);
     }
   }
+  // Output row k: reads input row k and writes output row k (so src and dst may alias). Row 2 of
+  // a two-row input is first rebuilt from rows 0 and 1 in pair arithmetic (rebuild_row2_pair).
+  template <int ES_IN = 1, int ES_OUT = 1>
+  __device__ __forceinline__ void apply_row(const V* src, V* dst, int k) const {
+    float xh[6], xl[6];
+    if (NE_IN == 6 && ROWS_OUT == 3 && k == 2) {
+      float uh[6], ul[6], vh[6], vl[6];
+      split_row<ES_IN>(src, 0, uh, ul);
+      split_row<ES_IN>(src, 1, vh, vl);
+      rebuild_row2_pair(uh, ul, vh, vl, xh, xl);
+    } else {
+      split_row<ES_IN>(src, k, xh, xl);
+    }
+    row_out<ES_OUT>(xh, xl, dst, k);
+  }
   template <int ES_IN = 1, int ES_OUT = 1>
   __device__ __forceinline__ void apply(const V* src, V* dst) const {
+    if constexpr (NE_IN == 6 && ROWS_OUT == 3) {
+      // two-row in, full out (never in place): rows 0 and 1 are split once and serve both their
+      // own outputs and the rebuild of row 2 (the same operations as apply_row, so the same bits)
+      float uh[6], ul[6], vh[6], vl[6], wh[6], wl[6];
+      split_row<ES_IN>(src, 0, uh, ul);
+      split_row<ES_IN>(src, 1, vh, vl);
+      rebuild_row2_pair(uh, ul, vh, vl, wh, wl);
+      row_out<ES_OUT>(uh, ul, dst, 0);
+      row_out<ES_OUT>(vh, vl, dst, 1);
+      row_out<ES_OUT>(wh, wl, dst, 2);
+    } else {
 #pragma unroll
-    for (int k = 0; k < ROWS_OUT; ++k) apply_row<ES_IN, ES_OUT>(src, dst, k);
+      for (int k = 0; k < ROWS_OUT; ++k) apply_row<ES_IN, ES_OUT>(src, dst, k);
+    }
   }
 };
 

@@ -143,6 +143,36 @@ def test_f32pair_generic_and_constant_inputs(h):
     assert np.max(np.abs(got[:, 0::2] - 1.0)) <= 1e-15 and np.max(np.abs(got[:, 1::2])) <= 1e-20
 
 
+@pytest.mark.parametrize("tpl", [1, 3])
+def test_f32pair_tworow_to_full_rebuild(h, tpl):
+    """Two-row in, full out, in FP32-pair arithmetic: row 2 of a is rebuilt as conj(row0 x row1)
+    from the pair splits of rows 0 and 1. On SU(3) input: within the FP64 form's 1e-13 of the
+    oracle. On rows of mixed magnitude (not SU(3)): against the oracle's FP64 expansion of the same
+    two rows, rows 0-1 within the product's 2^-42 sum_m |a_km||b_ml| and row 2 within
+    2^-40 sum_m S_m |b_ml|, S_m the moduli of the four products behind element m of row 2."""
+    cfg = {"tile_sites": 32, "stages": 3, "block": 128, "threads_per_link": tpl}
+    V = 3 * 8 ** 3 + 5
+    a, b = gen.lattice(17, V)
+    got = run_form(h, a, b, su3.F64, su3.TWOROW12, su3.FULL18, arith=su3.F32PAIR, cfg=cfg)
+    assert oracle.error(got, oracle.mult(a, b))[0] <= 1e-13
+    rng = np.random.default_rng(18)
+    V = 2000
+    a = rng.standard_normal(V * 72) * np.exp(rng.uniform(-10, 10, V * 72))
+    a = oracle.tworow_expand(oracle.tworow_compress(a))  # row 2 = conj(row0 x row1) in FP64
+    got = run_form(h, a, b, su3.F64, su3.TWOROW12, su3.FULL18, arith=su3.F32PAIR, cfg=cfg)
+    ref = oracle.mult(a, b)
+    A1 = np.abs(a).reshape(V, 4, 3, 3, 2).sum(-1)  # |re| + |im| of every element
+    B1 = np.abs(b).reshape(4, 3, 3, 2).sum(-1)
+    S = np.empty((V, 4, 3))
+    for m in range(3):
+        p, q = (m + 1) % 3, (m + 2) % 3
+        S[:, :, m] = A1[:, :, 0, p] * A1[:, :, 1, q] + A1[:, :, 0, q] * A1[:, :, 1, p]
+    bound = 2.0 ** -42 * np.einsum("sjkm,jml->sjkl", A1, B1)
+    bound[:, :, 2, :] = 2.0 ** -40 * np.einsum("sjm,jml->sjl", S, B1)
+    err = np.abs(got - ref).reshape(V, 4, 3, 3, 2)
+    assert np.all(err <= bound[..., None] + 1e-30)
+
+
 @pytest.mark.parametrize("layout", LAYOUTS, ids=["aos", "aosoa32", "soa"])
 @pytest.mark.parametrize("rep", [su3.FULL18, su3.TWOROW12], ids=["full", "2row"])
 def test_hybrid_is_native_or_pair_per_site(layout, rep):
