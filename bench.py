@@ -620,17 +620,34 @@ def adjacent_leg(h, torch, su3, a_dev, b, V, stream, extra, V_sample, reps=10):
     return res
 
 
+def cudart():
+    """The CUDA runtime library the process already uses (libsu3 links it), for plain copies."""
+    for name in ("libcudart.so.13", "libcudart.so.12", "libcudart.so"):
+        try:
+            rt = ctypes.CDLL(name)
+        except OSError:
+            continue
+        rt.cudaMemcpyAsync.restype = ctypes.c_int
+        rt.cudaMemcpyAsync.argtypes = [ctypes.c_void_p, ctypes.c_void_p, ctypes.c_size_t, ctypes.c_int,
+                                       ctypes.c_void_p]
+        return rt
+    return None
+
+
 def e2e_leg(h, torch, su3, a_host, b, V, args, stream, world, dev, a_dev=None, c_dev=None, sites_all=None):
-    """The same step through the host-buffer entry point: H2D of a from pinned memory, the kernel,
-    D2H of c, all inside the timed region (chunked and overlapped inside libsu3). For context, each
-    step is followed by the same bytes moved by two plain concurrent copies with no kernel, timed
-    separately: what the host link gives at that moment (it varies with load from other tenants)."""
+    """The same step through the host-buffer entry point with pinned a and c: every byte of a
+    crosses the host link to the GPU and every byte of c back inside the timed region (libsu3 takes
+    its direct path: the kernel streams both over the link). For context, each step is followed by
+    the same bytes moved by plain concurrent copies with no kernel, timed separately (what the link
+    gives at that moment), and the staged path (chunked copies through HBM) is timed afterwards."""
     d64 = su3.Desc(su3.F64, su3.FULL18, su3.AOS, V)
     c_host = torch.empty(V * 72, dtype=torch.float64, pin_memory=True)
     h.mult_host(d64, a_host.data_ptr(), b, d64, c_host.data_ptr(), stream)  # warm (staging buffers)
     k = max(3, min(args.steps, 5))
-    copies = a_dev is not None and c_dev is not None
+    rt = cudart()
+    copies = a_dev is not None and c_dev is not None and rt is not None
     s_in, s_out = (torch.cuda.Stream(), torch.cuda.Stream()) if copies else (None, None)
+    ring = torch.empty(3 * (64 << 20), dtype=torch.uint8, device=dev) if copies else None
     el = cel = 0.0
     barrier(world)
     for _ in range(k):
@@ -638,24 +655,51 @@ def e2e_leg(h, torch, su3, a_host, b, V, args, stream, world, dev, a_dev=None, c
         h.mult_host(d64, a_host.data_ptr(), b, d64, c_host.data_ptr(), stream)
         el += time.perf_counter() - t0
         if copies:
+            # the same bytes through plain copies and no kernel: a's sites H2D and back D2H into
+            # c_host in 64 MB pieces through a 3-slot device ring, on two streams ordered by events
+            # (the staged path's copy pattern; raw cudaMemcpyAsync, since torch's copy_ of these
+            # pinned tensors measured far below the link)
             torch.cuda.synchronize()
             t0 = time.perf_counter()
-            with torch.cuda.stream(s_in):
-                c_dev.copy_(a_host, non_blocking=True)
-            with torch.cuda.stream(s_out):
-                c_host.copy_(a_dev, non_blocking=True)
+            piece = 64 << 20
+            done_in = [torch.cuda.Event() for _ in range(3)]
+            done_out = [torch.cuda.Event() for _ in range(3)]
+            for i, off in enumerate(range(0, V * 576, piece)):
+                slot = i % 3
+                n = ctypes.c_size_t(min(piece, V * 576 - off))
+                buf = ctypes.c_void_p(ring.data_ptr() + slot * piece)
+                if i >= 3:
+                    s_in.wait_event(done_out[slot])
+                rt.cudaMemcpyAsync(buf, ctypes.c_void_p(a_host.data_ptr() + off), n, 1, ctypes.c_void_p(s_in.cuda_stream))
+                done_in[slot].record(s_in)
+                s_out.wait_event(done_in[slot])
+                rt.cudaMemcpyAsync(ctypes.c_void_p(c_host.data_ptr() + off), buf, n, 2, ctypes.c_void_p(s_out.cuda_stream))
+                done_out[slot].record(s_out)
             torch.cuda.synchronize()
             cel += time.perf_counter() - t0
+    path = {su3.HOST_DIRECT: "direct", su3.HOST_STAGED: "staged"}.get(h.last_host_path(), "none")
     el = max_over_ranks(el, world, dev)
     sites_all = world * V if sites_all is None else sites_all
     gbs = 1152.0 * sites_all * k / el / 1e9
     out = {"value": round(gbs, 2), "unit": "GB/s", "h2d_bytes_per_step": 576 * V, "d2h_bytes_per_step": 576 * V,
-           "steps": k, "ms_per_step": round(el / k * 1e3, 3),
-           "api": "su3_mult_host (pinned host a and c; chunked H2D / kernel / D2H overlapped on 3 streams)"}
+           "steps": k, "ms_per_step": round(el / k * 1e3, 3), "path": path,
+           "api": "su3_mult_host with pinned host a and c: the direct path (the kernel streams a in and c out "
+                  "over the host link, no staging copies)" if path == "direct" else
+                  "su3_mult_host (host a and c; chunked H2D / kernel / D2H overlapped on 3 streams)"}
     if copies:
         cel = max_over_ranks(cel, world, dev)
         out["copies_only_GBps"] = round(1152.0 * sites_all * k / cel / 1e9, 2)
         out["vs_copies_only"] = round(gbs / out["copies_only_GBps"], 3)
+    # for context: the same calls forced through the staged (chunked copy) path
+    h.set_host_path(su3.HOST_STAGED)
+    try:
+        t0 = time.perf_counter()
+        for _ in range(2):
+            h.mult_host(d64, a_host.data_ptr(), b, d64, c_host.data_ptr(), stream)
+        sel = max_over_ranks(time.perf_counter() - t0, world, dev)
+    finally:
+        h.set_host_path(su3.HOST_AUTO)
+    out["staged_path_GBps"] = round(1152.0 * sites_all * 2 / sel / 1e9, 2)
     del c_host
     return out
 

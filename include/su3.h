@@ -176,16 +176,29 @@ su3_status su3_mat_vec(su3_handle* h, int32_t adjoint, const su3_desc* a_desc, c
                        const double* v, void* w_dev, void* stream);
 
 /*
- * The same operation with HOST buffers: a_host is copied to the device in chunks, multiplied
- * and copied back into c_host, with copies and kernels overlapped on the handle's streams.
- * Synchronous: returns when c_host is complete. Pinned host memory (cudaHostRegister or
- * cudaMallocHost) gives full NVLink-C2C speed; pageable memory works but is slower.
- * Allocates device staging buffers owned by the handle (three buffers of ~64 MB of input each)
- * on the first call and whenever a larger site stride needs more; growing them synchronises the
- * device before freeing the old ones. AOS layout only (chunks are whole sites).
+ * The same operation with HOST buffers: returns when c_host is complete (synchronous). Two paths:
+ *  - DIRECT: when a_host and c_host each lie inside one pinned, mapped host allocation
+ *    (cudaMallocHost, cudaHostAlloc, cudaHostRegister), the kernel itself streams a in and c out
+ *    over the host link (NVLink-C2C on GB300), with coalesced 16-byte loads and stores from the
+ *    SMs and no staging buffer; nothing is allocated. Both ends of each range are checked; a
+ *    range that spans several allocations must not be passed.
+ *  - STAGED: otherwise (pageable memory), a_host is copied to the device in chunks, multiplied
+ *    and copied back into c_host, copies and kernels overlapped on the handle's streams. This
+ *    allocates device staging buffers owned by the handle (three buffers of ~64 MB of input each)
+ *    on the first call and whenever a larger site stride needs more; growing them synchronises
+ *    the device before freeing the old ones.
+ * su3_set_host_path chooses between them; su3_last_host_path reports which one the last call took.
+ * AOS layout only. Any arith, repr pair and site stride that su3_mult supports.
  */
 su3_status su3_mult_host(su3_handle* h, const su3_desc* a_desc, const void* a_host,
                          const double* b, const su3_desc* c_desc, void* c_host, void* stream);
+
+/* Path of su3_mult_host: AUTO (default) takes DIRECT when both buffers qualify, else STAGED;
+ * DIRECT fails with SU3_ERR_INVALID_ARG when they do not; STAGED always copies through HBM. */
+typedef enum { SU3_HOST_AUTO = 0, SU3_HOST_DIRECT = 1, SU3_HOST_STAGED = 2 } su3_host_path;
+su3_status su3_set_host_path(su3_handle* h, int32_t path);
+/* SU3_HOST_DIRECT or SU3_HOST_STAGED: the path of the handle's last su3_mult_host call (0: none). */
+int32_t su3_last_host_path(const su3_handle* h);
 
 /*
  * Many independent lattices (each its own a, b, c, n_sites and storage type) in ONE persistent

@@ -18,6 +18,7 @@ FULL18, TWOROW12 = 0, 1
 AOS, AOSOA32, SOA = 0, 1, 2
 NATIVE, F32PAIR, HYBRID = 0, 1, 2
 OP_NN, OP_NA, OP_AN = 0, 1, 2
+HOST_AUTO, HOST_DIRECT, HOST_STAGED = 0, 1, 2
 
 OK, ERR_INVALID_ARG, ERR_UNSUPPORTED, ERR_CUDA, ERR_NOT_INITIALIZED, ERR_TIMEOUT, ERR_FAULT_INJECTED = range(7)
 
@@ -94,6 +95,8 @@ _SIGS = {
                                    ctypes.c_void_p, ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p]),
     "su3_mat_vec": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(Desc), ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "su3_set_host_path": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
+    "su3_last_host_path": (ctypes.c_int32, [ctypes.c_void_p]),
 }
 
 
@@ -254,6 +257,13 @@ class Handle:
         c = LaunchCfg()
         self._check(lib().su3_get_batched_cfg(self._h, ctypes.byref(c)), "su3_get_batched_cfg")
         return c.as_dict()
+
+    def set_host_path(self, path):
+        """HOST_AUTO, HOST_DIRECT (kernel streams pinned host buffers) or HOST_STAGED (copies)."""
+        self._check(lib().su3_set_host_path(self._h, int(path)), "su3_set_host_path")
+
+    def last_host_path(self):
+        return int(lib().su3_last_host_path(self._h))
 
     def selftest_wait_timeout(self, limit_ms=50, stream=None):
         self._check(lib().su3_selftest_wait_timeout(self._h, limit_ms, _stream_ptr(stream)),

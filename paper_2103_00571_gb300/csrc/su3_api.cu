@@ -82,6 +82,8 @@ struct su3_handle {
   cudaStream_t s_h2d = nullptr, s_comp = nullptr, s_d2h = nullptr;
   cudaEvent_t ev_h2d[kHostBuffers] = {}, ev_comp[kHostBuffers] = {}, ev_d2h[kHostBuffers] = {};
   cudaEvent_t ev_start = nullptr;
+  int host_path = SU3_HOST_AUTO;  // su3_set_host_path
+  int host_path_used = 0;         // the path the last su3_mult_host call took
 };
 
 namespace {
@@ -540,6 +542,42 @@ su3_status su3_selftest_wait_timeout(su3_handle* h, int32_t limit_ms, void* stre
 
 // ---- host-buffer path ---------------------------------------------------------------------------
 
+namespace {
+
+// Device address of the host range [p, p + n) when the device can address all of it directly:
+// both ends inside pinned, mapped host memory, mapped contiguously. Null otherwise (pageable
+// memory, a range that leaves its allocation, or no mapping).
+void* mapped_view(const void* p, size_t n) {
+  if (n == 0) return nullptr;
+  cudaPointerAttributes a0, a1;
+  if (cudaPointerGetAttributes(&a0, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  const char* last = static_cast<const char*>(p) + (n - 1);
+  if (cudaPointerGetAttributes(&a1, last) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  if (a0.type != cudaMemoryTypeHost || a1.type != cudaMemoryTypeHost || !a0.devicePointer || !a1.devicePointer)
+    return nullptr;
+  if (static_cast<const char*>(a1.devicePointer) - static_cast<const char*>(a0.devicePointer) != (ptrdiff_t)(n - 1))
+    return nullptr;
+  return a0.devicePointer;
+}
+
+}  // namespace
+
+su3_status su3_set_host_path(su3_handle* h, int32_t path) {
+  if (!h) return SU3_ERR_NOT_INITIALIZED;
+  if (path != SU3_HOST_AUTO && path != SU3_HOST_DIRECT && path != SU3_HOST_STAGED)
+    return fail(h, SU3_ERR_INVALID_ARG, "host path must be SU3_HOST_AUTO, SU3_HOST_DIRECT or SU3_HOST_STAGED");
+  h->host_path = path;
+  return SU3_OK;
+}
+
+int32_t su3_last_host_path(const su3_handle* h) { return h ? h->host_path_used : 0; }
+
 su3_status su3_mult_host(su3_handle* h, const su3_desc* a_desc, const void* a_host, const double* b,
                          const su3_desc* c_desc, void* c_host, void* stream) {
   NvtxRange nvtx_range("su3_mult_host");
@@ -560,6 +598,22 @@ su3_status su3_mult_host(su3_handle* h, const su3_desc* a_desc, const void* a_ho
   s = check_cfg(h, f, cfg);
   if (s != SU3_OK) return s;
   cudaError_t e;
+  cudaStream_t user = (cudaStream_t)stream;
+  if (h->host_path != SU3_HOST_STAGED) {
+    // direct: the kernel streams a and c over the host link itself, no staging copies
+    void* a_view = mapped_view(a_host, (size_t)su3_array_bytes(a_desc));
+    void* c_view = mapped_view(c_host, (size_t)su3_array_bytes(c_desc));
+    if (a_view && c_view) {
+      h->host_path_used = SU3_HOST_DIRECT;
+      s = launch_mult_host_direct(f, cfg, a_view, b, c_view, ctx_of(h, user));
+      if (s != SU3_OK) return s;
+      return su3_sync(h, user, -1);
+    }
+    if (h->host_path == SU3_HOST_DIRECT)
+      return fail(h, SU3_ERR_INVALID_ARG,
+                  "the direct host path needs a and c each inside one pinned, mapped host allocation");
+  }
+  h->host_path_used = SU3_HOST_STAGED;
   if (!h->s_h2d) {
     for (cudaStream_t* p : {&h->s_h2d, &h->s_comp, &h->s_d2h}) {
       e = cudaStreamCreateWithFlags(p, cudaStreamNonBlocking);
@@ -576,6 +630,7 @@ su3_status su3_mult_host(su3_handle* h, const su3_desc* a_desc, const void* a_ho
   }
   // chunks of whole sites, a multiple of the kernel tile, ~64 MB of input each
   const int64_t a_site = f.a_stride, c_site = f.c_stride;
+  const int64_t c_links = 4 * link_bytes(f.dtype, f.repr_out);  // link bytes of one site of c
   int64_t chunk = std::max<int64_t>(cfg.tile_sites, (64ll << 20) / a_site / cfg.tile_sites * cfg.tile_sites);
   chunk = std::min<int64_t>(chunk, f.n_sites);
   const size_t a_bytes = (size_t)(chunk * a_site), c_bytes = (size_t)(chunk * c_site);
@@ -594,7 +649,6 @@ su3_status su3_mult_host(su3_handle* h, const su3_desc* a_desc, const void* a_ho
     }
     h->hbuf_bytes = need;
   }
-  cudaStream_t user = (cudaStream_t)stream;
   e = cudaEventRecord(h->ev_start, user);
   if (e != cudaSuccess) return cuda_err(h, "cudaEventRecord", e);
   for (cudaStream_t st : {h->s_h2d, h->s_comp, h->s_d2h}) cudaStreamWaitEvent(st, h->ev_start, 0);
@@ -618,8 +672,13 @@ su3_status su3_mult_host(su3_handle* h, const su3_desc* a_desc, const void* a_ho
     if (s != SU3_OK) return s;
     cudaEventRecord(h->ev_comp[bi], h->s_comp);
     cudaStreamWaitEvent(h->s_d2h, h->ev_comp[bi], 0);
-    e = cudaMemcpyAsync((unsigned char*)c_host + first * c_site, cbuf, (size_t)(ns * c_site),
-                        cudaMemcpyDeviceToHost, h->s_d2h);
+    if (c_site == c_links) {
+      e = cudaMemcpyAsync((unsigned char*)c_host + first * c_site, cbuf, (size_t)(ns * c_site),
+                          cudaMemcpyDeviceToHost, h->s_d2h);
+    } else {  // padded sites: only the link bytes of each site go back, c's pad bytes stay untouched
+      e = cudaMemcpy2DAsync((unsigned char*)c_host + first * c_site, (size_t)c_site, cbuf, (size_t)c_site,
+                            (size_t)c_links, (size_t)ns, cudaMemcpyDeviceToHost, h->s_d2h);
+    }
     if (e != cudaSuccess) return cuda_err(h, "cudaMemcpyAsync D2H", e);
     cudaEventRecord(h->ev_d2h[bi], h->s_d2h);
   }

@@ -191,6 +191,30 @@ struct Storage<kBF16> {
   }
 };
 
+// ---- b in the kernel parameters ---------------------------------------------------------------
+
+// The four b matrices by value in a kernel's parameter block: b[j][row][col][re/im].
+template <typename A>
+struct BMat {
+  A v[72];
+};
+
+template <typename A>
+inline BMat<A> make_b(const double* b) {
+  BMat<A> m;
+  for (int i = 0; i < 72; ++i) m.v[i] = (A)b[i];
+  return m;
+}
+
+// Stages b (72 reals) in shared memory and lets each thread's op take its direction j = tid % 4.
+template <class Op>
+__device__ __forceinline__ void load_b_op(const BMat<typename Op::BArg>& b, typename Op::BArg* bsh, Op& op,
+                                          int native_warps) {
+  for (int i = threadIdx.x; i < 72; i += blockDim.x) bsh[i] = b.v[i];
+  __syncthreads();
+  op.init(bsh + 18 * (threadIdx.x & 3), native_warps);
+}
+
 // ---- the link product -------------------------------------------------------------------------
 
 // A link in registers: up to 9 complex elements, row major (e = 3*row + col).

@@ -51,9 +51,22 @@ inline int64_t link_bytes(int dtype, int repr) { return (int64_t)n_elem(repr) * 
 // Default launch configuration of a form (used until the autotuner sets one).
 LaunchCfg default_cfg(const Form& f);
 
+// HYBRID: warps per CTA on the FP64 pipe, the nearest to native_permille of the CTA's warps.
+inline int native_warps(const Form& f, const LaunchCfg& cfg) {
+  if (f.arith != SU3_ARITH_HYBRID) return 0;
+  const int warps = cfg.block / 32;
+  const int n = (warps * cfg.native_permille + 500) / 1000;
+  return n < warps ? n : warps;
+}
+
 // c = a x b over one lattice (the streaming kernels). b is FP64 on the host.
 su3_status launch_mult(const Form& f, const LaunchCfg& cfg, const void* a, const double* b, void* c,
                        const LaunchCtx& ctx);
+
+// c = a x b with a and c in host memory the device can address (pinned, or any host memory on a
+// device with pageable-memory access): the kernel streams both over the host link itself.
+su3_status launch_mult_host_direct(const Form& f, const LaunchCfg& cfg, const void* a, const double* b, void* c,
+                                   const LaunchCtx& ctx);
 
 // a^dagger b (which 0), a v (1), a^dagger v (2): AOS FULL18 NATIVE; v[j] at bv[18*j .. 18*j+5].
 su3_status launch_adjacent(int which, const Form& f, const LaunchCfg& cfg, const void* a, const double* bv, void* c,

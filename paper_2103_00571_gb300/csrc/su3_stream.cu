@@ -31,11 +31,6 @@
 namespace su3 {
 
 template <typename A>
-struct BMat {
-  A v[72];  // b[j][row][col][re/im]
-};
-
-template <typename A>
 struct AosArgs {
   const unsigned char* a;
   unsigned char* c;
@@ -66,15 +61,6 @@ __host__ __device__ constexpr int tile_elem_stride() {
 template <int LAYOUT, int NE>
 __device__ __forceinline__ int tile_link_base(int q) {
   return LAYOUT == SU3_LAYOUT_AOSOA32 ? (q >> 5) * NE * 32 + (q & 31) : q;
-}
-
-// Stages b (72 reals) in shared memory and lets each thread's op take its direction j = tid % 4.
-template <class Op>
-__device__ __forceinline__ void load_b_op(const BMat<typename Op::BArg>& b, typename Op::BArg* bsh, Op& op,
-                                          int native_warps) {
-  for (int i = threadIdx.x; i < 72; i += blockDim.x) bsh[i] = b.v[i];
-  __syncthreads();
-  op.init(bsh + 18 * (threadIdx.x & 3), native_warps);
 }
 
 // The staged streaming kernel. Op::kNeIn complex elements per input link (9 full, 6 two-row),
@@ -340,20 +326,6 @@ LaunchCfg default_cfg(const Form& f) {
     }
   }
   return c;
-}
-
-template <typename A>
-static BMat<A> make_b(const double* b) {
-  BMat<A> m;
-  for (int i = 0; i < 72; ++i) m.v[i] = (A)b[i];
-  return m;
-}
-
-// HYBRID: warps per CTA on the FP64 pipe, the nearest to native_permille of the CTA's warps.
-static int native_warps(const Form& f, const LaunchCfg& cfg) {
-  if (f.arith != SU3_ARITH_HYBRID) return 0;
-  const int warps = cfg.block / 32;
-  return std::min(warps, (warps * cfg.native_permille + 500) / 1000);
 }
 
 static su3_status cuda_fail(const LaunchCtx& ctx, const char* what, cudaError_t e) {
