@@ -435,11 +435,11 @@ def run_native(args, world, rank, local):
         tr = traffic_record().get("su3_aos_kernel<%s,full>" % args.dtype, {})
         traffic = tr["bytes_per_site"] * V if tr and tr.get("source_digest") == source_digest() else None
         roofline = dict(hbm_roof, bound="hbm", traffic=traffic,
-                        kernel="su3_aos_kernel<NativeOp<%s,9,3>, %d>" % (args.dtype.upper(), tpl))
+                        kernel="su3_aos_kernel<NativeOp<%s,9,3>, %d, AOS>" % (args.dtype.upper(), tpl))
     elif args.arith == "native":
         roofline = {"bound": "alu", "achieved": round(achieved_tf, 4), "peak": round(fp64_peak, 4),
                     "unit": "TFLOP/s", "frac": round(achieved_tf / fp64_peak, 4), "traffic": traffic,
-                    "kernel": "su3_aos_kernel<NativeOp<F64,9,3>, %d>" % tpl,
+                    "kernel": "su3_aos_kernel<NativeOp<F64,9,3>, %d, AOS>" % tpl,
                     "peak_source": "FP64 pipe: %d SMs (this device) x 2 DFMA/clk x 2 flop x %.0f MHz (max SM clock)"
                                        % (sms, sm_max),
                     "hbm": hbm_roof}
@@ -447,8 +447,8 @@ def run_native(args, world, rank, local):
         tr = traffic_record().get("su3_aos_kernel<f64,full,%s>" % args.arith, {})
         traffic = tr["bytes_per_site"] * V if tr and tr.get("source_digest") == source_digest() else None
         roofline = dict(hbm_roof, bound="hbm", traffic=traffic,
-                        kernel="su3_aos_kernel<%s<9,3>, %d>" % ("PairF64Op" if args.arith == "f32pair" else "HybridF64Op",
-                                                                   tpl))
+                        kernel="su3_aos_kernel<%s<9,3>, %d, AOS>" % ("PairF64Op" if args.arith == "f32pair" else "HybridF64Op",
+                                                                        tpl))
 
     line = {"metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
