@@ -69,7 +69,7 @@ typedef enum { SU3_LAYOUT_AOS = 0, SU3_LAYOUT_AOSOA32 = 1, SU3_LAYOUT_SOA = 2 } 
  * into hi + lo with integer operations, exact TwoProduct/TwoSum transformations, error terms
  * accumulated in a second FP32 number, one FP64 add per output). GB300's FP64 units run at 1/64
  * of its FP32 rate, so this is several times faster. Accuracy: about 2^-45 times
- * sum_m |a[k][m]||b[m][l]| per output (measured max 3e-14 against the FP64 oracle on SU(3)
+ * sum_m |a[k][m]||b[m][l]| per output (measured max 3.3e-14 against the FP64 oracle on SU(3)
  * data, whose entries are <= 1). Valid for finite inputs with |x| < 2^127; input magnitudes below
  * 2^-74 (including zeros) act as values below 2^-73. All repr pairs are supported; for
  * TWOROW12 -> FULL18, row 2 of a is rebuilt as conj(row0 x row1) in FP32-pair arithmetic too

@@ -31,6 +31,7 @@ struct TileInfo {
 };
 
 struct BatchArgs {
+  float unit;  // 1.0 for FP32-pair arithmetic (a parameter, so the compiler cannot fold it)
   const BatchDesc* descs;
   int n;
   int total_tiles;
@@ -90,9 +91,10 @@ __device__ __forceinline__ void batch_tile_compute(unsigned char* in, int nt, co
 
 // FP64 lattice in FP32-pair arithmetic: b comes pre-split in the descriptor.
 template <int TPL>
-__device__ __forceinline__ void batch_tile_compute_pair(unsigned char* in, int nt, const BatchDesc& d) {
+__device__ __forceinline__ void batch_tile_compute_pair(unsigned char* in, int nt, const BatchDesc& d, float unit) {
   PairF64Op<9, 3> op;
   op.init_pre(d.bpair + 36 * (threadIdx.x & 3));
+  op.set_unit(unit);
   const int links = 4 * nt;
   for (int q = threadIdx.x; q < TPL * links; q += blockDim.x) {
     int row, link;
@@ -167,7 +169,7 @@ __global__ void __launch_bounds__(256) su3_batched_kernel(const __grid_constant_
     const int dtype = d.dtype;
     if (ok) {
       if (dtype == SU3_F64) {
-        if (d.arith == SU3_ARITH_F32PAIR) batch_tile_compute_pair<TPL>(in, ti.nt, d);
+        if (d.arith == SU3_ARITH_F32PAIR) batch_tile_compute_pair<TPL>(in, ti.nt, d, p.unit);
         else batch_tile_compute<kF64, TPL>(in, ti.nt, d);
       } else {
         batch_tile_compute<kF32, TPL>(in, ti.nt, d);
@@ -241,6 +243,7 @@ su3_status launch_batched(const BatchDesc* descs_dev, int n, int total_tiles, co
                           const LaunchCtx& ctx) {
   if (total_tiles == 0) return SU3_OK;
   BatchArgs p;
+  p.unit = 1.0f;
   p.descs = descs_dev;
   p.n = n;
   p.total_tiles = total_tiles;

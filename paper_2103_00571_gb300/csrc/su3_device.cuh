@@ -193,16 +193,20 @@ struct Storage<kBF16> {
 
 // ---- b in the kernel parameters ---------------------------------------------------------------
 
-// The four b matrices by value in a kernel's parameter block: b[j][row][col][re/im].
+// The four b matrices by value in a kernel's parameter block: b[j][row][col][re/im], plus the
+// constant 1.0 that FP32-pair arithmetic multiplies by (see dot_pair2: as a kernel parameter its
+// value is unknown to the compiler, so no multiply can be folded into the FMA that uses it).
 template <typename A>
 struct BMat {
   A v[72];
+  float unit;
 };
 
 template <typename A>
 inline BMat<A> make_b(const double* b) {
   BMat<A> m;
   for (int i = 0; i < 72; ++i) m.v[i] = (A)b[i];
+  m.unit = 1.0f;
   return m;
 }
 
@@ -213,6 +217,7 @@ __device__ __forceinline__ void load_b_op(const BMat<typename Op::BArg>& b, type
   for (int i = threadIdx.x; i < 72; i += blockDim.x) bsh[i] = b.v[i];
   __syncthreads();
   op.init(bsh + 18 * (threadIdx.x & 3), native_warps);
+  op.set_unit(b.unit);
 }
 
 // ---- the link product -------------------------------------------------------------------------
@@ -324,6 +329,7 @@ struct NativeOp {
   static constexpr bool kRowSplit = true;  // has apply_row: one thread per output row is possible
   A bre[9], bim[9];
   __device__ __forceinline__ void begin_tile(int) {}
+  __device__ __forceinline__ void set_unit(float) {}
   __device__ __forceinline__ void init(const BArg* bj, int /*native_warps*/) {
 #pragma unroll
     for (int e = 0; e < 9; ++e) {
@@ -380,6 +386,7 @@ struct AnOp {  // c[k][l] = sum_m conj(a[m][k]) b[m][l]
   static constexpr bool kRowSplit = false;  // row k of a^dagger b reads column k of a
   A bre[9], bim[9];
   __device__ __forceinline__ void begin_tile(int) {}
+  __device__ __forceinline__ void set_unit(float) {}
   __device__ __forceinline__ void init(const BArg* bj, int) {
 #pragma unroll
     for (int e = 0; e < 9; ++e) {
@@ -424,6 +431,7 @@ struct MatVecOp {  // w[k] = sum_m a[k][m] v[m]   (ADJ: sum_m conj(a[m][k]) v[m]
   static constexpr bool kRowSplit = false;  // one output vector per link
   A vre[3], vim[3];
   __device__ __forceinline__ void begin_tile(int) {}
+  __device__ __forceinline__ void set_unit(float) {}
   __device__ __forceinline__ void init(const BArg* vj, int) {
 #pragma unroll
     for (int m = 0; m < 3; ++m) {
@@ -505,45 +513,47 @@ __device__ __forceinline__ float2 fma2(float2 a, float2 b, float2 c) { return __
 __device__ __forceinline__ float2 sub2(float2 a, float2 b) { return __ffma2_rn(b, make_float2(-1.f, -1.f), a); }
 
 // The real and imaginary parts of one complex output as two lanes of FP32x2 operations:
-// sum_{t<N} x_t * y_t with x = (xh, xl) broadcast to both lanes and y = (yh, yl) per lane. The
-// error terms go to three independent accumulators (TwoSum errors, product errors, cross
-// products) so that no dependency chain is longer than two operations per term. The product
-// error x*y - p is one FMA with p negated in its operand (an exact sign flip that costs no
-// instruction; written as a subtraction from zero it cost one extra op per term, 3 % of the time).
+// sum_{t<N} x_t * y_t with x = (xh, xl) broadcast to both lanes and y = (yh, yl) per lane, in the
+// manner of Ogita, Rump and Oishi's Dot2. Per term t: the product p = fl(xh*yh), Knuth's TwoSum
+// s2 = s + p with its two exact error parts t1 (s's share) and t2 = p - z (p's share, z = s2 - s),
+// and the product error e = xh*yh - p. Since e and t2 are always added together and
+// e + t2 = xh*yh - z exactly, one FMA gives their sum with a single rounding of a value of size
+// ~ulp(s2) (so ~2^-48 of the sum); t1 and that FMA go to one error accumulator, the cross
+// products xh*yl + xl*yh to another. That is 10 FP32x2 operations per term instead of 12.
+// The add s + p is written as fma(p, unit, s) with unit = 1.0 passed as a kernel parameter: p's
+// only use is then inside an FMA's multiplicand, which the compiler cannot merge with p's multiply.
+// (As a plain add of a single-use product it was contracted into fma(xh, yh, s), which rounds
+// s2 differently from the TwoSum's p and loses the error term: ~2^-24 results, measured.)
 // The result is the unevaluated pair s + L per lane.
 template <int N>
 __device__ __forceinline__ void dot_pair2(const float (&xh)[N], const float (&xl)[N], const float2 (&yh)[N],
-                                          const float2 (&yl)[N], float2& s_out, float2& L_out) {
-  const float2 zero = make_float2(0.f, 0.f);
+                                          const float2 (&yl)[N], float2 one, float2& s_out, float2& L_out) {
   float2 x0h = make_float2(xh[0], xh[0]), x0l = make_float2(xl[0], xl[0]);
   float2 s = mul2(x0h, yh[0]);
-  float2 Le = fma2(x0h, yh[0], make_float2(-s.x, -s.y));
+  float2 Lt = fma2(x0h, yh[0], make_float2(-s.x, -s.y));  // e of the first product
   float2 Lc = fma2(x0h, yl[0], mul2(x0l, yh[0]));
-  float2 Lt = zero;
 #pragma unroll
   for (int t = 1; t < N; ++t) {
     const float2 xth = make_float2(xh[t], xh[t]), xtl = make_float2(xl[t], xl[t]);
     const float2 p = mul2(xth, yh[t]);
-    const float2 s2 = add2(s, p);
+    const float2 s2 = fma2(p, one, s);
     const float2 z = sub2(s2, s);
     const float2 t1 = sub2(s, sub2(s2, z));
-    const float2 t2 = sub2(p, z);
     s = s2;
     Lt = add2(Lt, t1);
-    Lt = add2(Lt, t2);
-    Le = add2(Le, fma2(xth, yh[t], make_float2(-p.x, -p.y)));
+    Lt = add2(Lt, fma2(xth, yh[t], make_float2(-z.x, -z.y)));  // e + t2 in one rounding
     Lc = fma2(xth, yl[t], Lc);
     Lc = fma2(xtl, yh[t], Lc);
   }
   s_out = s;
-  L_out = add2(add2(Lt, Le), Lc);
+  L_out = add2(Lt, Lc);
 }
 
 // One complex output of the product: the 6-term pair dot product, assembled into FP64.
 __device__ __forceinline__ double2 dot6_pair2(const float (&xh)[6], const float (&xl)[6], const float2 (&yh)[6],
-                                              const float2 (&yl)[6]) {
+                                              const float2 (&yl)[6], float2 one) {
   float2 s, L;
-  dot_pair2<6>(xh, xl, yh, yl, s, L);
+  dot_pair2<6>(xh, xl, yh, yl, one, s, L);
   return make_double2(f32_bits_to_f64(s.x) + f32_bits_to_f64(L.x), f32_bits_to_f64(s.y) + f32_bits_to_f64(L.y));
 }
 
@@ -557,7 +567,7 @@ __device__ __forceinline__ double2 dot6_pair2(const float (&xh)[6], const float 
 // The pair (s, L) of a Dot2 is itself a split of the value (s carries 24 bits, L the rest), so
 // row 2 goes into the product with no FP64 operation.
 __device__ __forceinline__ void rebuild_row2_pair(const float (&uh)[6], const float (&ul)[6], const float (&vh)[6],
-                                                  const float (&vl)[6], float (&wh)[6], float (&wl)[6]) {
+                                                  const float (&vl)[6], float2 one, float (&wh)[6], float (&wl)[6]) {
 #pragma unroll
   for (int k = 0; k < 3; ++k) {
     const int p = (k + 1) % 3, q = (k + 2) % 3;
@@ -568,7 +578,7 @@ __device__ __forceinline__ void rebuild_row2_pair(const float (&uh)[6], const fl
     const float2 yl[4] = {make_float2(vl[2 * q], -vl[2 * q + 1]), make_float2(-vl[2 * q + 1], -vl[2 * q]),
                           make_float2(-vl[2 * p], vl[2 * p + 1]), make_float2(vl[2 * p + 1], vl[2 * p])};
     float2 sv, Lv;
-    dot_pair2<4>(xh, xl, yh, yl, sv, Lv);
+    dot_pair2<4>(xh, xl, yh, yl, one, sv, Lv);
     wh[2 * k] = sv.x;
     wl[2 * k] = Lv.x;
     wh[2 * k + 1] = sv.y;
@@ -585,7 +595,9 @@ struct PairF64Op {
   // b[j] split once per thread, as lane pairs for the two terms of each (m, l):
   // (re, im) lanes of ar*(br, bi) and of ai*(-bi, br), high and low parts.
   float2 ya[9], yb[9], yla[9], ylb[9];
+  float2 one;  // (1, 1), from the kernel parameters (dot_pair2)
   __device__ __forceinline__ void begin_tile(int) {}
+  __device__ __forceinline__ void set_unit(float u) { one = make_float2(u, u); }
   __device__ __forceinline__ void init(const double* bj, int /*native_warps*/) {
 #pragma unroll
     for (int e = 0; e < 9; ++e) {
@@ -636,7 +648,7 @@ struct PairF64Op {
         yh[2 * m + 1] = yb[3 * m + l];
         yl[2 * m + 1] = ylb[3 * m + l];
       }
-      dst[(3 * k + l) * ES_OUT] = dot6_pair2(xh, xl, yh, yl);
+      dst[(3 * k + l) * ES_OUT] = dot6_pair2(xh, xl, yh, yl, one);
     }
   }
   // Output row k: reads input row k and writes output row k (so src and dst may alias). Row 2 of
@@ -648,7 +660,7 @@ struct PairF64Op {
       float uh[6], ul[6], vh[6], vl[6];
       split_row<ES_IN>(src, 0, uh, ul);
       split_row<ES_IN>(src, 1, vh, vl);
-      rebuild_row2_pair(uh, ul, vh, vl, xh, xl);
+      rebuild_row2_pair(uh, ul, vh, vl, one, xh, xl);
     } else {
       split_row<ES_IN>(src, k, xh, xl);
     }
@@ -662,7 +674,7 @@ struct PairF64Op {
       float uh[6], ul[6], vh[6], vl[6], wh[6], wl[6];
       split_row<ES_IN>(src, 0, uh, ul);
       split_row<ES_IN>(src, 1, vh, vl);
-      rebuild_row2_pair(uh, ul, vh, vl, wh, wl);
+      rebuild_row2_pair(uh, ul, vh, vl, one, wh, wl);
       row_out<ES_OUT>(uh, ul, dst, 0);
       row_out<ES_OUT>(vh, vl, dst, 1);
       row_out<ES_OUT>(wh, wl, dst, 2);
@@ -697,6 +709,7 @@ struct HybridF64Op {
   __device__ __forceinline__ void begin_tile(int k) {
     native = period > 0 && ((k + (int)(threadIdx.x >> 5)) % period) == 0;
   }
+  __device__ __forceinline__ void set_unit(float u) { pair.set_unit(u); }
   template <int ES_IN = 1, int ES_OUT = 1>
   __device__ __forceinline__ void apply(const V* src, V* dst) const {
     if (native) nat.template apply<ES_IN, ES_OUT>(src, dst);
