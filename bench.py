@@ -538,7 +538,7 @@ def forms_leg(h, torch, su3, a_dev, b, V, stream, f64_gbs, ref, V_sample, reps=1
         tol = TOL[(dt, 1 if (ri == 1 and ro == 1) or (ri == 1) else 0)]
         out[name] = {"GBps": round(gbs, 1), "site_updates_per_s": round(sups, 1),
                      "speedup_vs_f64": round(sups / f64_sups, 3), "max_err": err[0], "rms_err": err[1],
-                     "tol": tol, "ok": err[0] <= tol, "ms": round(per, 4), "launch_cfg": h.get_launch_cfg(da),
+                     "tol": tol, "ok": err[0] <= tol, "ms": round(per, 4), "launch_cfg": h.get_launch_cfg_for(da, dc),
                      "pack_GBps": round((576 * V + su3.array_bytes(da)) / (pack_ms * 1e-3) / 1e9, 1),
                      "unpack_GBps": round((su3.array_bytes(dc) + 576 * V) / (unpack_ms * 1e-3) / 1e9, 1)}
         if hbm_peak:

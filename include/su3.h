@@ -280,9 +280,17 @@ int64_t su3_array_bytes(const su3_desc* d);
 /* Validates a descriptor without touching the GPU (returns INVALID_ARG/UNSUPPORTED/OK). */
 su3_status su3_check_desc(const su3_desc* d);
 
-/* Per-form launch configuration used by su3_mult (the autotuner writes it). */
+/* Per-form launch configuration used by su3_mult (the autotuner writes it), for `form` as both a
+ * and c (same repr). su3_get_launch_cfg reports the configuration in force (the default if none
+ * was set). */
 su3_status su3_set_launch_cfg(su3_handle* h, const su3_desc* form, const su3_launch_cfg* cfg);
 su3_status su3_get_launch_cfg(su3_handle* h, const su3_desc* form, su3_launch_cfg* cfg);
+/* The same for one (a, c) repr pair: only c_form's repr is read. TWOROW12 -> FULL18 may take a
+ * launch shape of its own; without one it uses the TWOROW12 -> TWOROW12 configuration. */
+su3_status su3_set_launch_cfg_for(su3_handle* h, const su3_desc* a_form, const su3_desc* c_form,
+                                  const su3_launch_cfg* cfg);
+su3_status su3_get_launch_cfg_for(su3_handle* h, const su3_desc* a_form, const su3_desc* c_form,
+                                  su3_launch_cfg* cfg);
 
 /* Launch configuration of su3_mult_batched. A work tile is tile_sites * 576 bytes of input:
  * tile_sites sites of an F64 lattice or 2 * tile_sites sites of an F32 lattice. The cached graph

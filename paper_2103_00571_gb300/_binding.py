@@ -95,6 +95,10 @@ _SIGS = {
                                    ctypes.c_void_p, ctypes.POINTER(Desc), ctypes.c_void_p, ctypes.c_void_p]),
     "su3_mat_vec": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(Desc), ctypes.c_void_p,
                                    ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p]),
+    "su3_set_launch_cfg_for": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Desc), ctypes.POINTER(Desc),
+                                              ctypes.POINTER(LaunchCfg)]),
+    "su3_get_launch_cfg_for": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Desc), ctypes.POINTER(Desc),
+                                              ctypes.POINTER(LaunchCfg)]),
     "su3_set_host_path": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "su3_last_host_path": (ctypes.c_int32, [ctypes.c_void_p]),
 }
@@ -246,6 +250,19 @@ class Handle:
     def get_launch_cfg(self, form):
         c = LaunchCfg()
         self._check(lib().su3_get_launch_cfg(self._h, ctypes.byref(form), ctypes.byref(c)), "su3_get_launch_cfg")
+        return c.as_dict()
+
+    def set_launch_cfg_for(self, a_form, c_form, **cfg):
+        """Launch configuration of one (a, c) repr pair, e.g. two-row in, full out."""
+        c = LaunchCfg(cfg.get("block", 0), cfg.get("tile_sites", 0), cfg.get("stages", 0), cfg.get("ctas_per_sm", 0),
+                      cfg.get("native_permille", 0), cfg.get("threads_per_link", 0))
+        self._check(lib().su3_set_launch_cfg_for(self._h, ctypes.byref(a_form), ctypes.byref(c_form), ctypes.byref(c)),
+                    "su3_set_launch_cfg_for")
+
+    def get_launch_cfg_for(self, a_form, c_form):
+        c = LaunchCfg()
+        self._check(lib().su3_get_launch_cfg_for(self._h, ctypes.byref(a_form), ctypes.byref(c_form), ctypes.byref(c)),
+                    "su3_get_launch_cfg_for")
         return c.as_dict()
 
     def set_batched_cfg(self, **cfg):

@@ -59,7 +59,7 @@ struct su3_handle {
   int64_t launches = 0;
   std::string err;
   int fault = 0;
-  std::map<std::tuple<int, int, int, int, int>, LaunchCfg> cfgs;
+  std::map<std::tuple<int, int, int, int, int, int>, LaunchCfg> cfgs;  // CfgKey
   // batched, direct mode
   BatchDesc* bdesc_dev = nullptr;
   BatchDesc* bdesc_host = nullptr;  // pinned
@@ -111,14 +111,17 @@ LaunchCtx ctx_of(su3_handle* h, cudaStream_t st) {
   return c;
 }
 
-// Launch configurations are kept per (dtype, repr, layout, arith, padded): an AOS site stride
-// wider than the links (the paper's 640-byte FP64 site) needs more shared memory per site and
-// gets its own configuration.
-std::tuple<int, int, int, int, int> form_key(const su3_desc* d) {
+// Launch configurations are kept per (dtype, repr of a, repr of c, layout, arith, padded): an AOS
+// site stride wider than the links (the paper's 640-byte FP64 site) needs more shared memory per
+// site and gets its own configuration, and so does two-row in, full out (its kernel also keeps an
+// output ring and, in FP32 pairs, needs more registers than two-row in and out).
+using CfgKey = std::tuple<int, int, int, int, int, int>;
+CfgKey form_key(const su3_desc* d, int repr_out) {
   const bool padded = d->layout == SU3_LAYOUT_AOS && d->site_stride_bytes != 0 &&
                       d->site_stride_bytes != 4 * link_bytes(d->dtype, d->repr);
-  return std::make_tuple((int)d->dtype, (int)d->repr, (int)d->layout, (int)d->arith, padded ? 1 : 0);
+  return std::make_tuple((int)d->dtype, (int)d->repr, repr_out, (int)d->layout, (int)d->arith, padded ? 1 : 0);
 }
+CfgKey form_key(const su3_desc* d) { return form_key(d, d->repr); }
 
 int64_t resolved_stride(const su3_desc* d) {
   if (d->layout != SU3_LAYOUT_AOS) return 0;
@@ -151,8 +154,10 @@ su3_status check_cfg(su3_handle* h, const Form& f, const LaunchCfg& c) {
   return SU3_OK;
 }
 
+// The configuration of the (a, c) repr pair, else that of a's repr in and out, else the default.
 LaunchCfg cfg_for(su3_handle* h, const su3_desc* d, const Form& f) {
-  auto it = h->cfgs.find(form_key(d));
+  auto it = h->cfgs.find(form_key(d, f.repr_out));
+  if (it == h->cfgs.end() && f.repr_out != d->repr) it = h->cfgs.find(form_key(d));
   if (it != h->cfgs.end()) return it->second;
   return default_cfg(f);
 }
@@ -295,17 +300,32 @@ su3_status su3_finalize(su3_handle* h) {
   return SU3_OK;
 }
 
-su3_status su3_set_launch_cfg(su3_handle* h, const su3_desc* form, const su3_launch_cfg* cfg) {
+namespace {
+
+// The Form a configuration for (a_form -> repr_out) is validated against.
+su3_status cfg_form(su3_handle* h, const su3_desc* form, int repr_out, Form* f) {
+  if (su3_check_desc(form) != SU3_OK) return fail(h, SU3_ERR_INVALID_ARG, "invalid form descriptor");
+  if (repr_out != SU3_REPR_FULL18 && repr_out != SU3_REPR_TWOROW12)
+    return fail(h, SU3_ERR_INVALID_ARG, "invalid c representation");
+  if (form->repr == SU3_REPR_FULL18 && repr_out != SU3_REPR_FULL18)
+    return fail(h, SU3_ERR_UNSUPPORTED, "FULL18 input needs FULL18 output");
+  *f = Form{};
+  f->dtype = form->dtype;
+  f->repr_in = form->repr;
+  f->repr_out = repr_out;
+  f->layout = form->layout;
+  f->arith = form->arith;
+  f->n_sites = form->n_sites;
+  f->a_stride = f->c_stride = resolved_stride(form);
+  return SU3_OK;
+}
+
+su3_status set_cfg(su3_handle* h, const su3_desc* form, int repr_out, const su3_launch_cfg* cfg) {
   if (!h) return SU3_ERR_NOT_INITIALIZED;
   if (!form || !cfg) return fail(h, SU3_ERR_INVALID_ARG, "null form or cfg");
-  if (su3_check_desc(form) != SU3_OK) return fail(h, SU3_ERR_INVALID_ARG, "invalid form descriptor");
-  Form f{};
-  f.dtype = form->dtype;
-  f.repr_in = f.repr_out = form->repr;
-  f.layout = form->layout;
-  f.arith = form->arith;
-  f.n_sites = form->n_sites;
-  f.a_stride = f.c_stride = resolved_stride(form);
+  Form f;
+  su3_status s = cfg_form(h, form, repr_out, &f);
+  if (s != SU3_OK) return s;
   LaunchCfg c = default_cfg(f);
   if (cfg->block) c.block = cfg->block;
   if (cfg->tile_sites) c.tile_sites = cfg->tile_sites;
@@ -313,22 +333,18 @@ su3_status su3_set_launch_cfg(su3_handle* h, const su3_desc* form, const su3_lau
   if (cfg->ctas_per_sm) c.ctas_per_sm = cfg->ctas_per_sm;
   if (cfg->native_permille) c.native_permille = cfg->native_permille;
   if (cfg->threads_per_link) c.threads_per_link = cfg->threads_per_link;
-  su3_status s = check_cfg(h, f, c);
+  s = check_cfg(h, f, c);
   if (s != SU3_OK) return s;
-  h->cfgs[form_key(form)] = c;
+  h->cfgs[form_key(form, repr_out)] = c;
   return SU3_OK;
 }
 
-su3_status su3_get_launch_cfg(su3_handle* h, const su3_desc* form, su3_launch_cfg* cfg) {
+su3_status get_cfg(su3_handle* h, const su3_desc* form, int repr_out, su3_launch_cfg* cfg) {
   if (!h) return SU3_ERR_NOT_INITIALIZED;
-  if (!form || !cfg || su3_check_desc(form) != SU3_OK) return fail(h, SU3_ERR_INVALID_ARG, "invalid form or cfg");
-  Form f{};
-  f.dtype = form->dtype;
-  f.repr_in = f.repr_out = form->repr;
-  f.layout = form->layout;
-  f.arith = form->arith;
-  f.n_sites = form->n_sites;
-  f.a_stride = f.c_stride = resolved_stride(form);
+  if (!form || !cfg) return fail(h, SU3_ERR_INVALID_ARG, "null form or cfg");
+  Form f;
+  su3_status s = cfg_form(h, form, repr_out, &f);
+  if (s != SU3_OK) return s;
   LaunchCfg c = cfg_for(h, form, f);
   cfg->block = c.block;
   cfg->tile_sites = c.tile_sites;
@@ -337,6 +353,28 @@ su3_status su3_get_launch_cfg(su3_handle* h, const su3_desc* form, su3_launch_cf
   cfg->native_permille = c.native_permille;
   cfg->threads_per_link = c.threads_per_link;
   return SU3_OK;
+}
+
+}  // namespace
+
+su3_status su3_set_launch_cfg(su3_handle* h, const su3_desc* form, const su3_launch_cfg* cfg) {
+  return set_cfg(h, form, form ? form->repr : 0, cfg);
+}
+
+su3_status su3_get_launch_cfg(su3_handle* h, const su3_desc* form, su3_launch_cfg* cfg) {
+  return get_cfg(h, form, form ? form->repr : 0, cfg);
+}
+
+su3_status su3_set_launch_cfg_for(su3_handle* h, const su3_desc* a_form, const su3_desc* c_form,
+                                  const su3_launch_cfg* cfg) {
+  if (h && !c_form) return fail(h, SU3_ERR_INVALID_ARG, "null c form");
+  return set_cfg(h, a_form, c_form ? c_form->repr : 0, cfg);
+}
+
+su3_status su3_get_launch_cfg_for(su3_handle* h, const su3_desc* a_form, const su3_desc* c_form,
+                                  su3_launch_cfg* cfg) {
+  if (h && !c_form) return fail(h, SU3_ERR_INVALID_ARG, "null c form");
+  return get_cfg(h, a_form, c_form ? c_form->repr : 0, cfg);
 }
 
 su3_status su3_set_batched_cfg(su3_handle* h, const su3_launch_cfg* cfg) {

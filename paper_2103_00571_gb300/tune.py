@@ -11,8 +11,10 @@ count, and ``apply_cached`` installs them on a handle (bench.py and the tests us
     python -m paper_2103_00571_gb300.tune --time-batched 5 [--arith f32pair]   # time the batch only
 
 Form names are dtype-repr-layout[-arith][-p<stride>], e.g. f16-2row-aosoa32 or
-f64-full-aos-f32pair-p640 (the paper's padded 640-byte FP64 site). ``best_layout`` ranks the
-tuned layouts of a storage type, and ``apply_cached`` installs the configurations on a handle.
+f64-full-aos-f32pair-p640 (the paper's padded 640-byte FP64 site); repr is full (FULL18 in and
+out), 2row (TWOROW12 in and out) or 2to18 (TWOROW12 in, FULL18 out: its own launch shape, set
+with su3_set_launch_cfg_for). ``best_layout`` ranks the tuned layouts of a storage type, and
+``apply_cached`` installs the configurations on a handle.
 """
 import argparse
 import itertools
@@ -42,18 +44,28 @@ def form_name(desc):
     return name
 
 
-def parse_form(name, n_sites=0):
+def parse_pair(name, n_sites=0):
+    """(a form, c form) of a form name; the two differ only for 2to18 (two-row in, full out)."""
     parts = name.split("-")
     stride = 0
     if parts[-1].startswith("p") and parts[-1][1:].isdigit():
         stride = int(parts.pop()[1:])
     d, r, l, a = (parts + ["native"])[:4]
-    return B.Desc(DT[d], RP[r], LY[l], n_sites, stride, AR[a])
+    r_in, r_out = (B.TWOROW12, B.FULL18) if r == "2to18" else (RP[r], RP[r])
+    return (B.Desc(DT[d], r_in, LY[l], n_sites, stride, AR[a]), B.Desc(DT[d], r_out, LY[l], n_sites, stride, AR[a]))
+
+
+def parse_form(name, n_sites=0):
+    return parse_pair(name, n_sites)[0]
+
+
+def is_pair_name(name):
+    return "-2to18-" in name
 
 
 # The default grid. HYBRID forms (f64-*-hybrid) can still be named with --forms; they are left out
 # here because they measured slower than pure F32PAIR in every configuration tried.
-ALL_FORMS = ["f64-full-aos-f32pair",
+ALL_FORMS = ["f64-full-aos-f32pair", "f64-2to18-aos-f32pair", "f64-2to18-aos",
              "f64-full-aosoa32-f32pair", "f64-2row-aos-f32pair", "f64-full-aos", "f32-full-aos", "f16-full-aos", "bf16-full-aos", "f64-2row-aos", "f32-2row-aos",
              "f16-2row-aos", "f64-full-soa", "f32-full-soa", "f16-full-soa", "f64-full-aosoa32",
              "f32-full-aosoa32", "f16-full-aosoa32", "bf16-full-aosoa32",
@@ -79,7 +91,10 @@ def apply_cached(h, key=None):
     key = key or gpu_key()
     entry = cache.get(key, {})
     for name, cfg in entry.get("forms", {}).items():
-        h.set_launch_cfg(parse_form(name), **cfg["cfg"])
+        if is_pair_name(name):
+            h.set_launch_cfg_for(*parse_pair(name), **cfg["cfg"])
+        else:
+            h.set_launch_cfg(parse_form(name), **cfg["cfg"])
     if "batched" in entry:
         h.set_batched_cfg(**entry["batched"]["cfg"])
     return entry
@@ -96,6 +111,8 @@ def best_layout(dtype, repr_=None, arith=None, key=None):
     forms = load_cache().get(key, {}).get("forms", {})
     best = None
     for name, rec in forms.items():
+        if is_pair_name(name):
+            continue
         d = parse_form(name)
         if d.site_stride_bytes:  # padded AOS sites are a storage format, not a layout choice
             continue
@@ -104,7 +121,9 @@ def best_layout(dtype, repr_=None, arith=None, key=None):
     return None if best is None else best[1]
 
 
-def candidates(desc):
+def candidates(desc, out=None):
+    """Launch configurations to time for form `desc` (a), writing form `out` (c; default: desc)."""
+    out = desc if out is None else out
     if desc.arith == B.HYBRID:
         # one or two native warps per CTA; AOS tiles hold at least one link per thread
         out = []
@@ -114,7 +133,7 @@ def candidates(desc):
                 continue
             out += [dict(c, native_permille=nw * 1000 // warps) for nw in (1, 2) if nw < warps]
         return out
-    rows = 3 if desc.repr == B.FULL18 else 2  # output rows of the same-repr form
+    rows = 3 if out.repr == B.FULL18 else 2  # output rows: threads per link under the row split
     if desc.layout == B.AOS:
         site = desc.site_stride_bytes or B.link_bytes(desc.dtype, desc.repr) * 4
         out = []  # threads_per_link 3 = one thread per output row
@@ -147,19 +166,23 @@ def candidates(desc):
     return out
 
 
-def time_cfg(h, desc, abuf, b, cbuf, cfg, reps=5, iters=4):
+def time_cfg(h, desc, abuf, b, cbuf, cfg, reps=5, iters=4, out=None):
     import torch
-    h.set_launch_cfg(desc, **cfg)
+    out = desc if out is None else out
+    if out.repr != desc.repr:
+        h.set_launch_cfg_for(desc, out, **cfg)
+    else:
+        h.set_launch_cfg(desc, **cfg)
     s = torch.cuda.current_stream()
     for _ in range(2):
-        h.mult(desc, abuf, b, desc, cbuf)
+        h.mult(desc, abuf, b, out, cbuf)
     ts = []
     for _ in range(reps):
         e0 = torch.cuda.Event(enable_timing=True)
         e1 = torch.cuda.Event(enable_timing=True)
         e0.record(s)
         for _ in range(iters):
-            h.mult(desc, abuf, b, desc, cbuf)
+            h.mult(desc, abuf, b, out, cbuf)
         e1.record(s)
         e1.synchronize()
         ts.append(e0.elapsed_time(e1) / iters)
@@ -176,17 +199,16 @@ def tune_forms(h, names, L=48, log=print):
     b = gen.bmat(gen.DEFAULT_SEED, 0, V)
     results = {}
     for name in names:
-        d = parse_form(name, V)
-        nb = B.array_bytes(d)
-        abuf = torch.empty(nb, dtype=torch.uint8, device="cuda")
-        cbuf = torch.empty(nb, dtype=torch.uint8, device="cuda")
+        d, dc = parse_pair(name, V)
+        abuf = torch.empty(B.array_bytes(d), dtype=torch.uint8, device="cuda")
+        cbuf = torch.empty(B.array_bytes(dc), dtype=torch.uint8, device="cuda")
         h.pack(a64, d, abuf)
         best = None
-        for cfg in candidates(d):
-            ms = time_cfg(h, d, abuf, b, cbuf, cfg)
+        for cfg in candidates(d, dc):
+            ms = time_cfg(h, d, abuf, b, cbuf, cfg, out=dc)
             if best is None or ms < best[0]:
                 best = (ms, cfg)
-        gbs = (B.link_bytes(d.dtype, d.repr) * 8 * V) / (best[0] * 1e-3) / 1e9
+        gbs = ((B.link_bytes(d.dtype, d.repr) + B.link_bytes(dc.dtype, dc.repr)) * 4 * V) / (best[0] * 1e-3) / 1e9
         results[name] = {"cfg": best[1], "ms": round(best[0], 4), "GBps": round(gbs, 1), "L": L}
         log("%-22s %s  %.3f ms  %.0f GB/s" % (name, best[1], best[0], gbs))
         del abuf, cbuf

@@ -80,5 +80,11 @@ def test_form_names_round_trip():
     for name in tune.ALL_FORMS:
         d = tune.parse_form(name)
         assert tune.parse_form(tune.form_name(d)).key() == d.key()
+        a, c = tune.parse_pair(name)
+        assert a.key() == d.key()
+        assert (c.repr != a.repr) == tune.is_pair_name(name)
+    a, c = tune.parse_pair("f64-2to18-aos-f32pair")
+    assert (a.repr, c.repr, a.arith) == (su3.TWOROW12, su3.FULL18, su3.F32PAIR)
+    assert any(tune.is_pair_name(n) for n in tune.ALL_FORMS)
     d = tune.parse_form("f64-full-aos-f32pair-p640")
     assert (d.site_stride_bytes, d.arith) == (640, su3.F32PAIR) and tune.form_name(d) == "f64-full-aos-f32pair-p640"

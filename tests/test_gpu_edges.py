@@ -303,3 +303,27 @@ def test_launch_count(h):
     a, b = gen.lattice(8, V)
     run_form(h, a, b, su3.F64, iters=3)
     assert h.launch_count() - n0 == 5  # pack + 3 mult + unpack
+
+
+def test_launch_cfg_per_repr_pair():
+    """Two-row in, full out keeps a launch shape of its own (su3_set_launch_cfg_for); without one it
+    uses the two-row in and out shape. Every shape gives the same bits."""
+    h = su3.Handle(0)
+    V = 4 * 8 ** 3 + 3
+    a, b = gen.lattice(44, V)
+    for arith in (su3.NATIVE, su3.F32PAIR):
+        d2 = su3.Desc(su3.F64, su3.TWOROW12, su3.AOS, V, 0, arith)
+        df = su3.Desc(su3.F64, su3.FULL18, su3.AOS, V, 0, arith)
+        h.set_launch_cfg(d2, block=128, tile_sites=64, stages=3, ctas_per_sm=2, threads_per_link=1)
+        assert h.get_launch_cfg_for(d2, df)["tile_sites"] == 64  # falls back to the two-row shape
+        base = run_form(h, a, b, su3.F64, su3.TWOROW12, su3.FULL18, arith=arith)
+        h.set_launch_cfg_for(d2, df, block=256, tile_sites=24, stages=2, ctas_per_sm=1, threads_per_link=3)
+        assert h.get_launch_cfg_for(d2, df)["tile_sites"] == 24 and h.get_launch_cfg_for(d2, df)["threads_per_link"] == 3
+        assert h.get_launch_cfg(d2)["tile_sites"] == 64  # the two-row in/out shape is untouched
+        got = run_form(h, a, b, su3.F64, su3.TWOROW12, su3.FULL18, arith=arith)
+        assert np.array_equal(got, base)
+        assert oracle.error(got, oracle.mult(a, b))[0] <= 1e-12
+    with pytest.raises(su3.Su3Error):  # full in, two-row out is not a supported pair
+        h.set_launch_cfg_for(su3.Desc(su3.F64, su3.FULL18, su3.AOS, 8), su3.Desc(su3.F64, su3.TWOROW12, su3.AOS, 8),
+                             block=128)
+    h.close()
