@@ -425,6 +425,10 @@ def run_native(args, world, rank, local):
     fp64_peak = sms * 2 * 2 * sm_max * 1e6 / 1e12  # 2 DFMA/clk/SM x 2 flop x clock, TFLOP/s
     achieved_tf = FLOP_PER_SITE * V / (per_launch_ms * 1e-3) / 1e12
     achieved_gbs = bytes_per_step / (per_launch_ms * 1e-3) / 1e9
+    try:  # the FP64 pipe's sustained rate, measured on this device by a diagnostic FMA kernel
+        fp64_measured = h.measure_fp64_rate(8192)
+    except su3.Su3Error:
+        fp64_measured = None
     tr = traffic_record().get("su3_aos_kernel<f64,full>", {})
     traffic = None
     if tr and tr.get("source_digest") == source_digest():
@@ -442,6 +446,10 @@ def run_native(args, world, rank, local):
                     "kernel": "su3_aos_kernel<NativeOp<F64,9,3>, %d, AOS>" % tpl,
                     "peak_source": "FP64 pipe: %d SMs (this device) x 2 DFMA/clk x 2 flop x %.0f MHz (max SM clock)"
                                        % (sms, sm_max),
+                    "peak_measured": round(fp64_measured, 4) if fp64_measured else None,
+                    "frac_of_measured": round(achieved_tf / fp64_measured, 4) if fp64_measured else None,
+                    "peak_measured_source": "su3_measure_fp64_rate: 8 independent DFMA chains per thread, "
+                                            "2,048 threads per SM, CUDA events",
                     "hbm": hbm_roof}
     else:
         tr = traffic_record().get("su3_aos_kernel<f64,full,%s>" % args.arith, {})
@@ -488,6 +496,18 @@ def run_native(args, world, rank, local):
         line["forms"]["f64-aos-" + args.arith] = {"GBps": round(value / world, 1), "site_updates_per_s": round(sups / world, 1),
                                     "speedup_vs_f64": 1.0, "max_err": fp64_err[0], "rms_err": fp64_err[1],
                                     "tol": 1e-13, "ok": fp64_err[0] <= 1e-13}
+        # the fastest FP64-accurate form (FP64 in and out, within the FP64 tolerance) beside the
+        # plain method's headline: FP64 storage with FP32-pair arithmetic, AoS
+        fa = line["forms"].get("f64-f32pair-aos")
+        if fa:
+            tr = traffic_record().get("su3_aos_kernel<f64,full,f32pair>", {})
+            line["fp64_accurate"] = {
+                "form": "f64-f32pair-aos", "GBps": fa["GBps"], "site_updates_per_s": fa["site_updates_per_s"],
+                "speedup_vs_f64": fa["speedup_vs_f64"], "max_err": fa["max_err"], "tol": fa["tol"], "ok": fa["ok"],
+                "roofline": {"bound": "hbm", "achieved": fa["GBps"], "peak": hbm_peak, "unit": "GB/s",
+                             "frac": round(fa["GBps"] / hbm_peak, 4), "peak_source": peak_src + " hbm_gbs",
+                             "traffic": tr["bytes_per_site"] * V if tr and tr.get("source_digest") == source_digest() else None,
+                             "kernel": "su3_aos_kernel<PairF64Op<9,3>, 1, AOS>"}}
     if not args.quick:
         line["e2e"] = e2e_leg(h, torch, su3, a_host, b, V, args, stream, world, dev, a_dev, c_dev, sites_all)
         if rank == 0:

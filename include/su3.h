@@ -310,6 +310,15 @@ int64_t su3_launch_count(const su3_handle* h);
  */
 su3_status su3_selftest_wait_timeout(su3_handle* h, int32_t limit_ms, void* stream);
 
+/*
+ * Diagnostic (not part of the operation): the device's sustained FP64 fused multiply-add rate in
+ * TFLOP/s (2 flop per FMA), measured with 2,048 threads per SM each running 8 independent FMA
+ * chains of `steps` FMAs (1..2^24; ~8192 takes tens of milliseconds on GB300). It is the
+ * measured peak of the FP64 pipe that bounds the plain FP64 kernel. Synchronous; allocates a
+ * small scratch buffer for the duration of the call.
+ */
+su3_status su3_measure_fp64_rate(su3_handle* h, int32_t steps, double* tflops);
+
 int32_t su3_abi_version(void);
 
 #ifdef __cplusplus

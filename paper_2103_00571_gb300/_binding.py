@@ -99,6 +99,7 @@ _SIGS = {
                                               ctypes.POINTER(LaunchCfg)]),
     "su3_get_launch_cfg_for": (ctypes.c_int, [ctypes.c_void_p, ctypes.POINTER(Desc), ctypes.POINTER(Desc),
                                               ctypes.POINTER(LaunchCfg)]),
+    "su3_measure_fp64_rate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
     "su3_set_host_path": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "su3_last_host_path": (ctypes.c_int32, [ctypes.c_void_p]),
 }
@@ -274,6 +275,12 @@ class Handle:
         c = LaunchCfg()
         self._check(lib().su3_get_batched_cfg(self._h, ctypes.byref(c)), "su3_get_batched_cfg")
         return c.as_dict()
+
+    def measure_fp64_rate(self, steps=8192):
+        """Sustained FP64 FMA rate of the device in TFLOP/s (a diagnostic kernel)."""
+        out = ctypes.c_double()
+        self._check(lib().su3_measure_fp64_rate(self._h, int(steps), ctypes.byref(out)), "su3_measure_fp64_rate")
+        return out.value
 
     def set_host_path(self, path):
         """HOST_AUTO, HOST_DIRECT (kernel streams pinned host buffers) or HOST_STAGED (copies)."""

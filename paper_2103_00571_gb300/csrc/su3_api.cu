@@ -572,6 +572,31 @@ su3_status su3_sync(su3_handle* h, void* stream, int32_t timeout_ms) {
   return SU3_OK;
 }
 
+su3_status su3_measure_fp64_rate(su3_handle* h, int32_t steps, double* tflops) {
+  NvtxRange nvtx_range("su3_measure_fp64_rate");
+  if (!h) return SU3_ERR_NOT_INITIALIZED;
+  if (!tflops || steps < 1 || steps > (1 << 24)) return fail(h, SU3_ERR_INVALID_ARG, "steps must be in [1, 2^24]");
+  const int grid = h->num_sms * 8;  // 2,048 threads per SM
+  double* out = nullptr;
+  cudaError_t e = cudaMalloc((void**)&out, sizeof(double) * (size_t)grid * 256);
+  if (e != cudaSuccess) return cuda_err(h, "cudaMalloc", e);
+  cudaStream_t st = nullptr;
+  e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e != cudaSuccess) {
+    cudaFree(out);
+    return cuda_err(h, "cudaStreamCreate", e);
+  }
+  float ms = 0.f;
+  su3_status s = measure_dfma_rate(steps, out, grid, ctx_of(h, st), &ms);  // warm-up
+  if (s == SU3_OK) s = measure_dfma_rate(steps, out, grid, ctx_of(h, st), &ms);
+  cudaStreamDestroy(st);
+  cudaFree(out);
+  if (s != SU3_OK) return s;
+  // 8 chains per thread, 2 flop per FMA
+  *tflops = 2.0 * 8.0 * (double)grid * 256.0 * (double)steps / (ms * 1e-3) / 1e12;
+  return SU3_OK;
+}
+
 su3_status su3_selftest_wait_timeout(su3_handle* h, int32_t limit_ms, void* stream) {
   if (!h) return SU3_ERR_NOT_INITIALIZED;
   if (limit_ms < 1 || limit_ms > 2000) return fail(h, SU3_ERR_INVALID_ARG, "limit_ms must be in [1, 2000]");

@@ -28,6 +28,8 @@ def test_quick_line_has_the_contract_keys():
     for k in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
         assert k in r, k
     assert r["bound"] == "alu" and 0 < r["frac"] < 1.2 and "hbm" in r
+    # the FP64 pipe's rate measured on the device, beside the derived peak
+    assert 0.3 < r["peak_measured"] < 3.0 and 0 < r["frac_of_measured"] < 1.3
     assert "workload" in d["config"] and d["config"]["lattice"] == "16^4"
     assert set(d["clocks"]) >= {"sm_mhz", "sm_max_mhz", "reasons"}
 
@@ -37,3 +39,9 @@ def test_launch_override_and_reduced_dtype():
                   "--launch", "block=128,tile_sites=32,stages=3,ctas_per_sm=2,threads_per_link=3")
     assert d["roofline"]["bound"] == "hbm" and d["config"]["tuned"] is False
     assert d["config"]["launch_cfg"]["threads_per_link"] == 3 and d["config"]["launch_cfg"]["tile_sites"] == 32
+
+
+def test_shard_mode_line():
+    """--shard at N = 1: the one slab is the whole lattice; the line says strong scaling."""
+    d = run_bench("--quick", "--shard", "--L", "16", "--steps", "3", "--warmup", "3")
+    assert d["scaling"] == "strong" and d["value"] > 0 and d["config"]["parallelism"] == "single GPU"

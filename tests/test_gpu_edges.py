@@ -327,3 +327,12 @@ def test_launch_cfg_per_repr_pair():
         h.set_launch_cfg_for(su3.Desc(su3.F64, su3.FULL18, su3.AOS, 8), su3.Desc(su3.F64, su3.TWOROW12, su3.AOS, 8),
                              block=128)
     h.close()
+
+
+def test_measure_fp64_rate(h):
+    """The FP64 FMA-rate diagnostic: a plausible rate for a GB300 (about 1.25 TFLOP/s nominal) and
+    argument checks."""
+    tf = h.measure_fp64_rate(2048)
+    assert 0.3 < tf < 3.0, tf
+    with pytest.raises(su3.Su3Error):
+        h.measure_fp64_rate(0)
