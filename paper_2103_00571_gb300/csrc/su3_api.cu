@@ -22,6 +22,13 @@
 
 using namespace su3;
 
+namespace su3 {
+// Times `grid` CTAs of 256 threads, each thread running 8 independent FP64 FMA chains of `steps`
+// FMAs (diagnostic: the device's sustained FP64 FMA rate); out_dev holds grid * 256 doubles.
+// Defined in su3_diag.cu.
+su3_status measure_dfma_rate(int steps, double* out_dev, int grid, const LaunchCtx& ctx, float* ms);
+}  // namespace su3
+
 namespace {
 
 // NVTX range over one entry point: names the call in Nsight timelines and in ncu's NVTX

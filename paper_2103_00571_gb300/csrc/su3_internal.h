@@ -75,10 +75,6 @@ su3_status launch_adjacent(int which, const Form& f, const LaunchCfg& cfg, const
 // One CTA whose bounded mbarrier wait runs out after limit_ms (failure-path self test).
 su3_status launch_selftest_wait(int limit_ms, const LaunchCtx& ctx);
 
-// Times `grid` CTAs of 256 threads, each thread running 8 independent FP64 FMA chains of `steps`
-// FMAs (diagnostic: the device's sustained FP64 FMA rate); out_dev holds grid * 256 doubles.
-su3_status measure_dfma_rate(int steps, double* out_dev, int grid, const LaunchCtx& ctx, float* ms);
-
 // Packed FP64 AOS <-> the form's storage.
 su3_status launch_pack(const Form& dst, const double* src, void* dst_dev, const LaunchCtx& ctx);
 su3_status launch_unpack(const Form& src, const void* src_dev, double* dst, const LaunchCtx& ctx);
