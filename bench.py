@@ -606,9 +606,10 @@ def adjacent_leg(h, torch, su3, a_dev, b, V, stream, extra, V_sample, reps=10):
     site-updates/s, algorithmic GB/s (link bytes read + output bytes written) and error."""
     res = {}
     vec = torch.empty(V * 24, dtype=torch.float64, device=a_dev.device)
-    for dt, dname in ((su3.F64, "f64"), (su3.F32, "f32")):
+    for dt, dname, arith in ((su3.F64, "f64", su3.NATIVE), (su3.F64, "f64-f32pair", su3.F32PAIR),
+                             (su3.F32, "f32", su3.NATIVE)):
         rb = 8 if dt == su3.F64 else 4
-        d = su3.Desc(dt, su3.FULL18, su3.AOS, V)
+        d = su3.Desc(dt, su3.FULL18, su3.AOS, V, 0, arith)
         abuf = a_dev if dt == su3.F64 else torch.empty(su3.array_bytes(d), dtype=torch.uint8, device=a_dev.device)
         if dt != su3.F64:
             h.pack(a_dev, d, abuf, stream)

@@ -156,7 +156,8 @@ su3_status su3_mult(su3_handle* h, const su3_desc* a_desc, const void* a_dev,
  *   SU3_OP_NN: c = a x b           (exactly su3_mult)
  *   SU3_OP_NA: c = a x b^dagger    (b^dagger formed exactly on the host, then the su3_mult path;
  *                                    every form su3_mult supports)
- *   SU3_OP_AN: c = a^dagger x b    (its own kernel: AOS, FULL18 -> FULL18, NATIVE, any dtype)
+ *   SU3_OP_AN: c = a^dagger x b    (its own kernel: AOS, FULL18 -> FULL18, NATIVE for any dtype
+ *                                    or F32PAIR for F64)
  * Same conventions as su3_mult (asynchronous, caller-owned 16-byte-aligned device buffers).
  */
 typedef enum { SU3_OP_NN = 0, SU3_OP_NA = 1, SU3_OP_AN = 2 } su3_op;
@@ -166,7 +167,8 @@ su3_status su3_mult_op(su3_handle* h, int32_t op, const su3_desc* a_desc, const 
 /*
  * Matrix x colour vector (MILC's mult_su3_mat_vec; with adjoint != 0 its adjoint form):
  *   w[i][j][k] = sum_m a[i][j][k][m] v[j][m]        or   sum_m conj(a[i][j][m][k]) v[j][m].
- * a: AOS FULL18 NATIVE array of any dtype (packed or strided sites); v: host FP64
+ * a: AOS FULL18 array of any dtype, NATIVE arithmetic (or F32PAIR for F64; packed or strided
+ * sites); v: host FP64
  * double v[4][3][2], one colour vector per link direction, copied at call time (rounded once to
  * FP32 for F32/F16/BF16 storage); w_dev: packed array of n_sites x 4 colour vectors (3 complex
  * each) in a's dtype, n_sites * 12 * 2 * sizeof(real) bytes, caller-owned, not overlapping a.

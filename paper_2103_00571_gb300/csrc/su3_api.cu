@@ -464,8 +464,8 @@ su3_status su3_mult_op(su3_handle* h, int32_t op, const su3_desc* a_desc, const 
   su3_status s = make_form(h, a_desc, c_desc, &f);
   if (s != SU3_OK) return s;
   if (f.layout != SU3_LAYOUT_AOS || f.repr_in != SU3_REPR_FULL18 || f.repr_out != SU3_REPR_FULL18 ||
-      f.arith != SU3_ARITH_NATIVE)
-    return fail(h, SU3_ERR_UNSUPPORTED, "a^dagger b takes AOS FULL18 arrays with NATIVE arithmetic");
+      (f.arith != SU3_ARITH_NATIVE && !(f.arith == SU3_ARITH_F32PAIR && f.dtype == SU3_F64)))
+    return fail(h, SU3_ERR_UNSUPPORTED, "a^dagger b takes AOS FULL18 arrays with NATIVE arithmetic (or F32PAIR for F64)");
   if (f.n_sites == 0) return SU3_OK;
   if (!a_dev || !c_dev || !aligned16(a_dev) || !aligned16(c_dev))
     return fail(h, SU3_ERR_INVALID_ARG, "null or misaligned a or c");
@@ -491,8 +491,9 @@ su3_status su3_mat_vec(su3_handle* h, int32_t adjoint, const su3_desc* a_desc, c
   Form f;
   su3_status s = make_form(h, a_desc, a_desc, &f);
   if (s != SU3_OK) return s;
-  if (f.layout != SU3_LAYOUT_AOS || f.repr_in != SU3_REPR_FULL18 || f.arith != SU3_ARITH_NATIVE)
-    return fail(h, SU3_ERR_UNSUPPORTED, "matrix x vector takes AOS FULL18 arrays with NATIVE arithmetic");
+  if (f.layout != SU3_LAYOUT_AOS || f.repr_in != SU3_REPR_FULL18 ||
+      (f.arith != SU3_ARITH_NATIVE && !(f.arith == SU3_ARITH_F32PAIR && f.dtype == SU3_F64)))
+    return fail(h, SU3_ERR_UNSUPPORTED, "matrix x vector takes AOS FULL18 arrays with NATIVE arithmetic (or F32PAIR for F64)");
   if (f.n_sites == 0) return SU3_OK;
   f.c_stride = 12 * 2 * real_bytes(f.dtype);  // 4 packed colour vectors per site
   if (!a_dev || !w_dev || !aligned16(a_dev) || !aligned16(w_dev))

@@ -689,6 +689,84 @@ struct PairF64Op {
 };
 
 
+// The adjacent products in FP32-pair arithmetic (FP64 storage, FP64-accurate results):
+// a^dagger b, whose output row k is the product's row routine applied to column k of a
+// conjugated (the imaginary parts' splits change sign, exactly), with the same b pairs.
+struct PairAnOp {
+  using V = double2;
+  using BArg = double;
+  static constexpr int kNeIn = 9, kNeOut = 9;
+  static constexpr bool kRowSplit = false;  // row k of a^dagger b reads column k of a
+  PairF64Op<9, 3> pair;                     // b as FP32 pairs and the row routine
+  __device__ __forceinline__ void begin_tile(int) {}
+  __device__ __forceinline__ void set_unit(float u) { pair.set_unit(u); }
+  __device__ __forceinline__ void init(const double* bj, int w) { pair.init(bj, w); }
+  template <int ES_IN = 1, int ES_OUT = 1>
+  __device__ __forceinline__ void apply(const V* src, V* dst) const {
+    double2 a[9];  // all of a first: the output may overwrite it (in place)
+#pragma unroll
+    for (int e = 0; e < 9; ++e) a[e] = src[e * ES_IN];
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float xh[6], xl[6];  // conj(a[m][k]), terms 2m: re, 2m+1: im
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const FF re = split_f64(a[3 * m + k].x), im = split_f64(a[3 * m + k].y);
+        xh[2 * m] = re.h;
+        xl[2 * m] = re.l;
+        xh[2 * m + 1] = -im.h;
+        xl[2 * m + 1] = -im.l;
+      }
+      pair.template row_out<ES_OUT>(xh, xl, dst, k);
+    }
+  }
+};
+
+// a v and a^dagger v in FP32-pair arithmetic: each output element is one 6-term pair dot product
+// of row k of a (ADJ: column k, conjugated) with v[j] held as FP32 pairs.
+template <bool ADJ>
+struct PairMatVecOp {
+  using V = double2;
+  using BArg = double;
+  static constexpr int kNeIn = 9, kNeOut = 3;
+  static constexpr bool kRowSplit = false;  // one output vector per link
+  float2 ya[3], yb[3], yla[3], ylb[3];      // v[m]: (re, im), (-im, re), and their low parts
+  float2 one;
+  __device__ __forceinline__ void begin_tile(int) {}
+  __device__ __forceinline__ void set_unit(float u) { one = make_float2(u, u); }
+  __device__ __forceinline__ void init(const double* vj, int) {
+#pragma unroll
+    for (int m = 0; m < 3; ++m) {
+      const double r = vj[2 * m], i = vj[2 * m + 1];
+      const float rh = __double2float_rn(r), ih = __double2float_rn(i);
+      const float rl = __double2float_rn(r - (double)rh), il = __double2float_rn(i - (double)ih);
+      ya[m] = make_float2(rh, ih);
+      yb[m] = make_float2(-ih, rh);
+      yla[m] = make_float2(rl, il);
+      ylb[m] = make_float2(-il, rl);
+    }
+  }
+  template <int ES_IN = 1, int ES_OUT = 1>
+  __device__ __forceinline__ void apply(const V* src, V* dst) const {
+    const float2 yh[6] = {ya[0], yb[0], ya[1], yb[1], ya[2], yb[2]};
+    const float2 yl[6] = {yla[0], ylb[0], yla[1], ylb[1], yla[2], ylb[2]};
+#pragma unroll
+    for (int k = 0; k < 3; ++k) {
+      float xh[6], xl[6];
+#pragma unroll
+      for (int m = 0; m < 3; ++m) {
+        const double2 v = src[(ADJ ? 3 * m + k : 3 * k + m) * ES_IN];
+        const FF re = split_f64(v.x), im = split_f64(v.y);
+        xh[2 * m] = re.h;
+        xl[2 * m] = re.l;
+        xh[2 * m + 1] = ADJ ? -im.h : im.h;
+        xl[2 * m + 1] = ADJ ? -im.l : im.l;
+      }
+      dst[k * ES_OUT] = dot6_pair2(xh, xl, yh, yl, one);
+    }
+  }
+};
+
 // HYBRID: per tile, warp w uses the FP64 pipe (NATIVE) when (tile + w) % period == 0 and FP32
 // pairs otherwise, period = warps / native_warps. The native work rotates over all warps, so it
 // is spread over every SM sub-partition's FP64 unit. Each thread keeps both forms of its b[j].

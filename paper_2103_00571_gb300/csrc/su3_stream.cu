@@ -499,13 +499,19 @@ su3_status launch_mult(const Form& f, const LaunchCfg& cfg, const void* a, const
 }
 
 // a^dagger x b (which = 0), a v (1) and a^dagger v (2) over an AOS FULL18 array (NATIVE
-// arithmetic). For the matrix x vector forms `bv` holds v[j] at bv[18*j .. 18*j+5] and c is the
+// arithmetic, or FP32 pairs for FP64 storage). For the matrix x vector forms `bv` holds v[j] at bv[18*j .. 18*j+5] and c is the
 // packed array of output colour vectors (4 per site).
 su3_status launch_adjacent(int which, const Form& f, const LaunchCfg& cfg, const void* a, const double* bv, void* c,
                            const LaunchCtx& ctx) {
-  if (f.layout != SU3_LAYOUT_AOS || f.repr_in != SU3_REPR_FULL18 || f.arith != SU3_ARITH_NATIVE) {
-    *ctx.err = "adjacent operations take AOS FULL18 arrays with NATIVE arithmetic";
+  const bool pair = f.arith == SU3_ARITH_F32PAIR && f.dtype == SU3_F64;
+  if (f.layout != SU3_LAYOUT_AOS || f.repr_in != SU3_REPR_FULL18 || (f.arith != SU3_ARITH_NATIVE && !pair)) {
+    *ctx.err = "adjacent operations take AOS FULL18 arrays with NATIVE arithmetic (or F32PAIR for F64)";
     return SU3_ERR_UNSUPPORTED;
+  }
+  if (pair) {
+    if (which == 0) return run_aos<PairAnOp>(f, cfg, a, bv, c, ctx);
+    if (which == 1) return run_aos<PairMatVecOp<false>>(f, cfg, a, bv, c, ctx);
+    return run_aos<PairMatVecOp<true>>(f, cfg, a, bv, c, ctx);
   }
 #define SU3_ADJ_CASES(DT)                                                             \
   case DT:                                                                            \

@@ -115,3 +115,59 @@ def test_adjacent_rejects(h):
         h.mat_vec(da, buf, np.zeros(24), buf.data_ptr() + 16)  # overlapping output
     assert e.value.status == 1
     h.sync()
+
+
+@pytest.mark.parametrize("V", SIZES)
+def test_adjacent_in_fp32_pairs(h, V):
+    """a b^dagger, a^dagger b, a v and a^dagger v with FP64 storage and FP32-pair arithmetic: within
+    the FP64 tolerance of the oracle, also on padded 640-byte sites and in place (a^dagger b)."""
+    a, b = gen.lattice(15, V)
+    d = su3.Desc(su3.F64, su3.FULL18, su3.AOS, V, 0, su3.F32PAIR)
+    abuf = to_dev(a)
+    for op, ref in ((su3.OP_NA, oracle.mult_na(a, b)), (su3.OP_AN, oracle.mult_an(a, b))):
+        cbuf = to_dev(np.zeros_like(a))
+        h.mult_op(op, d, abuf, b, d, cbuf)
+        h.sync()
+        assert oracle.error(cbuf.cpu().numpy(), ref)[0] <= 1e-13, op
+    v = np.random.default_rng(V + 1).standard_normal(24) / 2.0
+    for adjoint in (False, True):
+        w = empty_bytes(V * 24 * 8 + 4096, fill=0x33)
+        h.mat_vec(d, abuf, v, w, adjoint=adjoint)
+        h.sync()
+        raw = w.cpu().numpy()
+        assert np.all(raw[V * 24 * 8:] == 0x33)
+        assert oracle.error(raw[: V * 24 * 8].view(np.float64), oracle.mat_vec(a, v, adjoint=adjoint))[0] <= 1e-13
+    # padded sites, and a^dagger b in place
+    a640 = np.zeros((V, 80))
+    a640[:, :72] = a.reshape(V, 72)
+    d640 = su3.Desc(su3.F64, su3.FULL18, su3.AOS, V, 640, su3.F32PAIR)
+    buf = to_dev(a640.reshape(-1))
+    h.mult_op(su3.OP_AN, d640, buf, b, d640, buf)
+    h.sync()
+    got = buf.cpu().numpy().reshape(V, 80)
+    assert np.all(got[:, 72:] == 0.0)
+    assert oracle.error(got[:, :72].reshape(-1), oracle.mult_an(a, b))[0] <= 1e-13
+
+
+def test_adjacent_pairs_generic_magnitudes(h):
+    """a^dagger b and a v in FP32 pairs on entries of mixed magnitude: within 2^-42 of the sum of
+    |x||y| over each output's six real terms (the same relative bound as the product)."""
+    rng = np.random.default_rng(16)
+    V = 2000
+    a = rng.standard_normal(V * 72) * np.exp(rng.uniform(-15, 15, V * 72))
+    _, b = gen.lattice(16, V)
+    d = su3.Desc(su3.F64, su3.FULL18, su3.AOS, V, 0, su3.F32PAIR)
+    abuf = to_dev(a)
+    c = to_dev(np.zeros_like(a))
+    h.mult_op(su3.OP_AN, d, abuf, b, d, c)
+    v = rng.standard_normal(24)
+    w = to_dev(np.zeros(V * 24))
+    h.mat_vec(d, abuf, v, w)
+    h.sync()
+    A = np.abs(a).reshape(V, 4, 3, 3, 2).sum(-1)
+    B = np.abs(b).reshape(4, 3, 3, 2).sum(-1)
+    bound_an = np.einsum("sjmk,jml->sjkl", A, B).repeat(2, axis=-1).reshape(-1)
+    assert np.all(np.abs(c.cpu().numpy() - oracle.mult_an(a, b)) <= 2.0 ** -42 * bound_an + 1e-30)
+    Vv = np.abs(v).reshape(4, 3, 2).sum(-1)
+    bound_mv = np.einsum("sjkm,jm->sjk", A, Vv).repeat(2, axis=-1).reshape(-1)
+    assert np.all(np.abs(w.cpu().numpy() - oracle.mat_vec(a, v)) <= 2.0 ** -42 * bound_mv + 1e-30)

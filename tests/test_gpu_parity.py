@@ -197,3 +197,26 @@ def test_hybrid_is_native_or_pair_per_site(layout, rep):
     mx, _ = oracle.error(got.reshape(-1), oracle.mult(a, b))
     assert mx <= tol(su3.F64, rep)
     hh.close()
+
+
+@pytest.mark.parametrize("arith", [su3.NATIVE, su3.F32PAIR], ids=["native", "f32pair"])
+@pytest.mark.parametrize("rep", [su3.FULL18, su3.TWOROW12], ids=["full", "2row-to-full"])
+def test_total_cancellation_gives_identity(h, arith, rep):
+    """a[i][j] = b[j]^dagger for every site: c = b^dagger b = I exactly. Each off-diagonal output is a
+    sum of O(1) terms that cancels to zero and each diagonal output is exactly 1, the case in which
+    a lost or doubly counted error term of the FP32-pair sums would show. Against the exact I,
+    within the FP64 tolerance."""
+    V = 777
+    _, b = gen.lattice(61, V)
+    bj = b.reshape(4, 3, 3, 2)
+    bdag = np.empty_like(bj)
+    bdag[..., 0] = np.transpose(bj[..., 0], (0, 2, 1))
+    bdag[..., 1] = -np.transpose(bj[..., 1], (0, 2, 1))
+    a = np.tile(bdag.reshape(-1), V)
+    ident = np.zeros((4, 3, 3, 2))
+    for k in range(3):
+        ident[:, k, k, 0] = 1.0
+    want = np.tile(ident.reshape(-1), V)
+    assert oracle.error(oracle.mult(a, b), want)[0] <= 1e-14  # the oracle agrees: b is unitary
+    got = run_form(h, a, b, su3.F64, rep, su3.FULL18, arith=arith)
+    assert oracle.error(got, want)[0] <= 1e-13
