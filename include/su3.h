@@ -28,7 +28,7 @@
 extern "C" {
 #endif
 
-#define SU3_ABI_VERSION 2
+#define SU3_ABI_VERSION 3
 
 typedef enum {
   SU3_OK = 0,
@@ -65,10 +65,11 @@ typedef enum { SU3_LAYOUT_AOS = 0, SU3_LAYOUT_AOSOA32 = 1, SU3_LAYOUT_SOA = 2 } 
 
 /*
  * Arithmetic of the F64 storage type. NATIVE: FP64 fused multiply-adds (the plain method).
- * F32PAIR: FP64 storage, arithmetic on unevaluated pairs of FP32 numbers (each a element split
- * into hi + lo with integer operations, exact TwoProduct/TwoSum transformations, error terms
- * accumulated in a second FP32 number, one FP64 add per output). GB300's FP64 units run at 1/64
- * of its FP32 rate, so this is several times faster. Accuracy: about 2^-45 times
+ * F32PAIR: FP64 storage, arithmetic on unevaluated pairs of FP32 numbers. Each a element is split
+ * into hi + lo with integer operations; each output real is a compensated dot product (TwoSum on
+ * the running FP32 sum, the product error and the product's share of the TwoSum error added by one
+ * FMA, error terms accumulated in a second FP32 number) and becomes FP64 with one FP64 add.
+ * GB300's FP64 units run at 1/64 of its FP32 rate, so this is several times faster. Accuracy: about 2^-45 times
  * sum_m |a[k][m]||b[m][l]| per output (measured max 3.3e-14 against the FP64 oracle on SU(3)
  * data, whose entries are <= 1). Valid for finite inputs with |x| < 2^127; input magnitudes below
  * 2^-74 (including zeros) act as values below 2^-73. All repr pairs are supported; for
