@@ -150,14 +150,22 @@ def dist_setup(args):
         import torch.distributed as dist
         os.environ.setdefault("MASTER_ADDR", "127.0.0.1")
         backend = "nccl" if args.impl == "native" else "gloo"
+        if backend == "nccl":
+            # each rank's GPU must be current before NCCL binds the process group to a device
+            import torch
+            torch.cuda.set_device(local)
         dist.init_process_group(backend)
     return world, rank, local
 
 
 def barrier(world):
     if world > 1:
+        import torch
         import torch.distributed as dist
-        dist.barrier()
+        if dist.get_backend() == "nccl":
+            dist.barrier(device_ids=[torch.cuda.current_device()])
+        else:
+            dist.barrier()
 
 
 def max_over_ranks(x, world, device=None):
