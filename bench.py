@@ -13,7 +13,8 @@ batched 96-lattice workload, the end-to-end host-buffer path and the CPU oracle 
 Under torchrun (N > 1) every rank runs its own L=64 lattice (replicas: sites are independent, no
 data-path collective; weak scaling); only the timing uses a barrier and a max over ranks. With
 --shard the ranks instead split ONE L=64 lattice into contiguous slabs of sites (strong scaling,
-still without a data-path collective).
+still without a data-path collective). The CPU baseline, the per-form, batched and adjacent-op legs
+run at N = 1 only; at N > 1 the line carries the timed step and the end-to-end leg.
 """
 import os
 
@@ -491,8 +492,9 @@ def run_native(args, world, rank, local):
             "launch_ms": {"mean": round(per_launch_ms, 4), "median": round(launch_ms[len(launch_ms) // 2], 4),
                           "min": round(launch_ms[0], 4), "max": round(launch_ms[-1], 4)}}
 
-    if rank == 0 and not args.quick:
-        # CPU baseline leg (oracle, as it stands, on the host cores; bounded sample)
+    if world == 1 and not args.quick:
+        # CPU baseline leg (oracle, as it stands, on the host cores; bounded sample) and the
+        # per-form legs: single-GPU runs only, so that N > 1 holds its GPUs for the timed step alone
         V_sample = min(V, 1 << 20)
         cpu, ref, extra = cpu_baseline_leg(a_host.numpy(), b, V_sample)
         line["cpu_baseline"] = cpu
@@ -518,7 +520,7 @@ def run_native(args, world, rank, local):
                              "kernel": "su3_aos_kernel<PairF64Op<9,3>, 1, AOS>"}}
     if not args.quick:
         line["e2e"] = e2e_leg(h, torch, su3, a_host, b, V, args, stream, world, dev, a_dev, c_dev, sites_all)
-        if rank == 0:
+        if world == 1:
             line["batched"] = batched_leg(h, torch, su3, gen, extra["batched"])
     elif rank == 0:
         line["e2e"] = None
