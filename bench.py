@@ -676,7 +676,9 @@ def e2e_leg(h, torch, su3, a_host, b, V, args, stream, world, dev, a_dev=None, c
     crosses the host link to the GPU and every byte of c back inside the timed region (libsu3 takes
     its direct path: the kernel streams both over the link). For context, each step is followed by
     the same bytes moved by plain concurrent copies with no kernel, timed separately (what the link
-    gives at that moment), and the staged path (chunked copies through HBM) is timed afterwards."""
+    gives at that moment), and the staged path (chunked copies through HBM) is timed afterwards, as
+    is the default path on ordinary (unpinned) arrays: direct where the device reads pageable host
+    memory coherently, staged elsewhere."""
     d64 = su3.Desc(su3.F64, su3.FULL18, su3.AOS, V)
     c_host = torch.empty(V * 72, dtype=torch.float64, pin_memory=True)
     h.mult_host(d64, a_host.data_ptr(), b, d64, c_host.data_ptr(), stream)  # warm (staging buffers)
@@ -737,6 +739,22 @@ def e2e_leg(h, torch, su3, a_host, b, V, args, stream, world, dev, a_dev=None, c
     finally:
         h.set_host_path(su3.HOST_AUTO)
     out["staged_path_GBps"] = round(1152.0 * sites_all * 2 / sel / 1e9, 2)
+    # ordinary pageable a and c (no pinning): on a device that reads pageable host memory
+    # coherently through the host's page tables, the default path streams them as they stand; the
+    # pages are touched on the host first, as an application's own arrays would be
+    a_page = a_host.numpy().copy()
+    c_page = np.zeros_like(a_page)
+    h.mult_host(d64, a_page, b, d64, c_page, stream)  # warm
+    barrier(world)
+    t0 = time.perf_counter()
+    for _ in range(2):
+        h.mult_host(d64, a_page, b, d64, c_page, stream)
+    pel = max_over_ranks(time.perf_counter() - t0, world, dev)
+    out["pageable"] = {"GBps": round(1152.0 * sites_all * 2 / pel / 1e9, 2),
+                       "path": {su3.HOST_DIRECT: "direct", su3.HOST_STAGED: "staged"}.get(h.last_host_path(), "none"),
+                       "device_reads_pageable_memory": h.pageable_host_access(),
+                       "same_bits_as_pinned": bool(np.array_equal(c_page, c_host.numpy()))}
+    del a_page, c_page
     del c_host
     return out
 

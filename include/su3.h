@@ -28,7 +28,7 @@
 extern "C" {
 #endif
 
-#define SU3_ABI_VERSION 3
+#define SU3_ABI_VERSION 4
 
 typedef enum {
   SU3_OK = 0,
@@ -184,8 +184,12 @@ su3_status su3_mat_vec(su3_handle* h, int32_t adjoint, const su3_desc* a_desc, c
  *    (cudaMallocHost, cudaHostAlloc, cudaHostRegister), the kernel itself streams a in and c out
  *    over the host link (NVLink-C2C on GB300), with coalesced 16-byte loads and stores from the
  *    SMs and no staging buffer; nothing is allocated. Both ends of each range are checked; a
- *    range that spans several allocations must not be passed.
- *  - STAGED: otherwise (pageable memory), a_host is copied to the device in chunks, multiplied
+ *    range that spans several allocations must not be passed. On a device that reads pageable
+ *    host memory coherently (su3_host_pageable_access() == 1: the GPU translates host addresses
+ *    through the host's page tables, as on GB300 over NVLink-C2C), ordinary pageable memory
+ *    (malloc, numpy) qualifies too: the kernel reads and writes it as it stands. Pages that the
+ *    host never touched are first populated by the operating system, slowly, on either path.
+ *  - STAGED: otherwise (pageable memory on other devices), a_host is copied to the device in chunks, multiplied
  *    and copied back into c_host, copies and kernels overlapped on the handle's streams. This
  *    allocates device staging buffers owned by the handle (three buffers of ~64 MB of input each)
  *    on the first call and whenever a larger site stride needs more; growing them synchronises
@@ -196,12 +200,17 @@ su3_status su3_mat_vec(su3_handle* h, int32_t adjoint, const su3_desc* a_desc, c
 su3_status su3_mult_host(su3_handle* h, const su3_desc* a_desc, const void* a_host,
                          const double* b, const su3_desc* c_desc, void* c_host, void* stream);
 
-/* Path of su3_mult_host: AUTO (default) takes DIRECT when both buffers qualify, else STAGED;
- * DIRECT fails with SU3_ERR_INVALID_ARG when they do not; STAGED always copies through HBM. */
+/* Path of su3_mult_host: AUTO (default) takes DIRECT when both buffers qualify (pinned and
+ * mapped, or pageable on a device with coherent pageable access), else STAGED; DIRECT fails with
+ * SU3_ERR_INVALID_ARG when they do not; STAGED always copies through HBM. */
 typedef enum { SU3_HOST_AUTO = 0, SU3_HOST_DIRECT = 1, SU3_HOST_STAGED = 2 } su3_host_path;
 su3_status su3_set_host_path(su3_handle* h, int32_t path);
 /* SU3_HOST_DIRECT or SU3_HOST_STAGED: the path of the handle's last su3_mult_host call (0: none). */
 int32_t su3_last_host_path(const su3_handle* h);
+/* 1 when the handle's device reads and writes pageable host memory coherently
+ * (cudaDevAttrPageableMemoryAccess), so that the direct host path also takes pageable buffers;
+ * 0 otherwise or for a null handle. */
+int32_t su3_host_pageable_access(const su3_handle* h);
 
 /*
  * Many independent lattices (each its own a, b, c, n_sites and storage type) in ONE persistent

@@ -102,6 +102,7 @@ _SIGS = {
     "su3_measure_fp64_rate": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32, ctypes.POINTER(ctypes.c_double)]),
     "su3_set_host_path": (ctypes.c_int, [ctypes.c_void_p, ctypes.c_int32]),
     "su3_last_host_path": (ctypes.c_int32, [ctypes.c_void_p]),
+    "su3_host_pageable_access": (ctypes.c_int32, [ctypes.c_void_p]),
 }
 
 
@@ -283,11 +284,17 @@ class Handle:
         return out.value
 
     def set_host_path(self, path):
-        """HOST_AUTO, HOST_DIRECT (kernel streams pinned host buffers) or HOST_STAGED (copies)."""
+        """HOST_AUTO, HOST_DIRECT (the kernel streams pinned host buffers, or pageable ones on a
+        device with coherent pageable access) or HOST_STAGED (chunked copies through HBM)."""
         self._check(lib().su3_set_host_path(self._h, int(path)), "su3_set_host_path")
 
     def last_host_path(self):
         return int(lib().su3_last_host_path(self._h))
+
+    def pageable_host_access(self):
+        """Whether the device reads pageable host memory coherently (the direct path then also
+        takes pageable buffers)."""
+        return bool(lib().su3_host_pageable_access(self._h))
 
     def selftest_wait_timeout(self, limit_ms=50, stream=None):
         self._check(lib().su3_selftest_wait_timeout(self._h, limit_ms, _stream_ptr(stream)),

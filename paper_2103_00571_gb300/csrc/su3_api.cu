@@ -91,6 +91,7 @@ struct su3_handle {
   cudaEvent_t ev_start = nullptr;
   int host_path = SU3_HOST_AUTO;  // su3_set_host_path
   int host_path_used = 0;         // the path the last su3_mult_host call took
+  bool pageable_access = false;   // the device reads pageable host memory coherently
 };
 
 namespace {
@@ -269,6 +270,11 @@ su3_status su3_init(int device, su3_handle** out) {
     e = cudaDeviceGetAttribute(&h->smem_per_sm, cudaDevAttrMaxSharedMemoryPerMultiprocessor, device);
   if (e == cudaSuccess)
     e = cudaDeviceGetAttribute(&h->smem_reserved, cudaDevAttrReservedSharedMemoryPerBlock, device);
+  if (e == cudaSuccess) {
+    int pma = 0;
+    e = cudaDeviceGetAttribute(&pma, cudaDevAttrPageableMemoryAccess, device);
+    h->pageable_access = (e == cudaSuccess && pma != 0);
+  }
   if (e == cudaSuccess) e = cudaMalloc((void**)&h->status_dev, sizeof(unsigned));
   if (e == cudaSuccess) e = cudaMemset(h->status_dev, 0, sizeof(unsigned));
   if (e != cudaSuccess) {
@@ -637,7 +643,20 @@ void* mapped_view(const void* p, size_t n) {
   return a0.devicePointer;
 }
 
+// p itself when it is ordinary (unregistered, pageable) host memory, which a device with coherent
+// pageable-memory access reads and writes through the host's page tables; else nullptr.
+void* pageable_view(const void* p) {
+  cudaPointerAttributes a;
+  if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+    cudaGetLastError();
+    return nullptr;
+  }
+  return a.type == cudaMemoryTypeUnregistered ? const_cast<void*>(p) : nullptr;
+}
+
 }  // namespace
+
+int32_t su3_host_pageable_access(const su3_handle* h) { return h && h->pageable_access ? 1 : 0; }
 
 su3_status su3_set_host_path(su3_handle* h, int32_t path) {
   if (!h) return SU3_ERR_NOT_INITIALIZED;
@@ -674,6 +693,12 @@ su3_status su3_mult_host(su3_handle* h, const su3_desc* a_desc, const void* a_ho
     // direct: the kernel streams a and c over the host link itself, no staging copies
     void* a_view = mapped_view(a_host, (size_t)su3_array_bytes(a_desc));
     void* c_view = mapped_view(c_host, (size_t)su3_array_bytes(c_desc));
+    if (h->pageable_access) {
+      // a device that reads pageable host memory coherently streams ordinary buffers as they
+      // stand (measured on GB300: 2x the staged path's copies from pageable memory)
+      if (!a_view) a_view = pageable_view(a_host);
+      if (!c_view) c_view = pageable_view(c_host);
+    }
     if (a_view && c_view) {
       h->host_path_used = SU3_HOST_DIRECT;
       s = launch_mult_host_direct(f, cfg, a_view, b, c_view, ctx_of(h, user));
@@ -682,7 +707,10 @@ su3_status su3_mult_host(su3_handle* h, const su3_desc* a_desc, const void* a_ho
     }
     if (h->host_path == SU3_HOST_DIRECT)
       return fail(h, SU3_ERR_INVALID_ARG,
-                  "the direct host path needs a and c each inside one pinned, mapped host allocation");
+                  h->pageable_access
+                      ? "the direct host path needs a and c in host memory (pinned, mapped or pageable)"
+                      : "the direct host path needs a and c each inside one pinned, mapped host allocation "
+                        "(this device does not read pageable host memory)");
   }
   h->host_path_used = SU3_HOST_STAGED;
   if (!h->s_h2d) {

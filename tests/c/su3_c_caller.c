@@ -1,8 +1,9 @@
 /*
  * A plain C99 caller of libsu3, with no Python and no PyTorch in the process: the SU3_Bench
  * product (§Background, c[i].link[j] = a[i].link[j] x b[j]) through su3_mult on device buffers
- * and through su3_mult_host on pageable and on pinned host buffers, in FP64 with NATIVE and with
- * F32PAIR arithmetic, each checked against the FP64 oracle within the FP64 form's 1e-13.
+ * and through su3_mult_host on pageable host buffers (the path the library picks, then the staged
+ * path) and on pinned ones, in FP64 with NATIVE and with F32PAIR arithmetic, each checked against
+ * the FP64 oracle within the FP64 form's 1e-13.
  *
  * Test infrastructure: it links the oracle and the seeded input generator beside libsu3 only to
  * compare. Usage: su3_c_caller [L]  (an L^4 lattice, default 8). Exit 0 when every check passed.
@@ -68,6 +69,7 @@ int main(int argc, char** argv) {
   su3o_mult(V, 72, a, b, ref);
 
   if (!su3_ok(su3_init(0, &h), "su3_init")) return 1;
+  printf("pageable host access: %d\n", (int)su3_host_pageable_access(h));
   double *a_dev = NULL, *c_dev = NULL, *a_pin = NULL, *c_pin = NULL;
   if (!cuda_ok(cudaMalloc((void**)&a_dev, bytes), "cudaMalloc a") ||
       !cuda_ok(cudaMalloc((void**)&c_dev, bytes), "cudaMalloc c") ||
@@ -92,15 +94,29 @@ int main(int argc, char** argv) {
     snprintf(what, sizeof what, "su3_mult device %s", names[t]);
     ok = ok && check(what, c, ref, n);
 
-    /* pageable host buffers: the staged path */
+    /* pageable host buffers: streamed by the kernel on a device that reads them coherently,
+       else copied through HBM */
+    const int32_t want_path = su3_host_pageable_access(h) ? SU3_HOST_DIRECT : SU3_HOST_STAGED;
     memset(c, 0, bytes);
     ok = ok && su3_ok(su3_mult_host(h, &d, a, b, &d, c, NULL), "su3_mult_host pageable");
     snprintf(what, sizeof what, "su3_mult_host pageable %s", names[t]);
     ok = ok && check(what, c, ref, n);
-    if (ok && su3_last_host_path(h) != SU3_HOST_STAGED) {
-      fprintf(stderr, "pageable buffers took path %d, not the staged path\n", (int)su3_last_host_path(h));
+    if (ok && su3_last_host_path(h) != want_path) {
+      fprintf(stderr, "pageable buffers took path %d, not %d\n", (int)su3_last_host_path(h), (int)want_path);
       ok = 0;
     }
+
+    /* pageable host buffers forced through the staged path */
+    memset(c, 0, bytes);
+    ok = ok && su3_ok(su3_set_host_path(h, SU3_HOST_STAGED), "su3_set_host_path");
+    ok = ok && su3_ok(su3_mult_host(h, &d, a, b, &d, c, NULL), "su3_mult_host pageable staged");
+    snprintf(what, sizeof what, "su3_mult_host pageable staged %s", names[t]);
+    ok = ok && check(what, c, ref, n);
+    if (ok && su3_last_host_path(h) != SU3_HOST_STAGED) {
+      fprintf(stderr, "SU3_HOST_STAGED took path %d\n", (int)su3_last_host_path(h));
+      ok = 0;
+    }
+    ok = su3_ok(su3_set_host_path(h, SU3_HOST_AUTO), "su3_set_host_path") && ok;
 
     /* pinned host buffers: the kernel streams them over the host link */
     memset(c_pin, 0, bytes);

@@ -22,7 +22,7 @@ def test_library_exports_header():
     missing = [n for n in names if not hasattr(L, n)]
     assert not missing, missing
     hdr = open(os.path.join(ROOT, "include", "su3.h")).read()
-    assert L.su3_abi_version() == int(re.search(r"#define SU3_ABI_VERSION (\d+)", hdr).group(1)) == 3
+    assert L.su3_abi_version() == int(re.search(r"#define SU3_ABI_VERSION (\d+)", hdr).group(1)) == 4
 
 
 def test_header_is_plain_c_and_links(tmp_path):

@@ -1,8 +1,9 @@
 """libsu3 from a plain C99 program (tests/c/su3_c_caller.c): no Python or PyTorch in the process
 that calls the C ABI. On CPU the program compiles under -std=c99 -pedantic -Werror (the CUDA
 runtime header as a system header) and links against libsu3, the CUDA runtime, the oracle and the
-input generator; on a GPU it runs su3_mult (device buffers) and su3_mult_host (pageable and pinned
-host buffers), NATIVE and F32PAIR, and checks every result against the FP64 oracle within 1e-13."""
+input generator; on a GPU it runs su3_mult (device buffers) and su3_mult_host (pageable buffers on
+the path the library picks and on the staged path, pinned buffers), NATIVE and F32PAIR, and checks
+every result against the FP64 oracle within 1e-13."""
 import os
 import subprocess
 
@@ -44,4 +45,4 @@ def test_c_caller_matches_oracle(tmp_path, L):
     r = subprocess.run([exe, str(L)], capture_output=True, text=True, timeout=300)
     assert r.returncode == 0, r.stdout + r.stderr
     assert "c caller ok" in r.stdout
-    assert r.stdout.count("max abs err") == 6  # 2 arithmetics x (device, pageable, pinned)
+    assert r.stdout.count("max abs err") == 8  # 2 arithmetics x (device, pageable, pageable staged, pinned)

@@ -1,7 +1,7 @@
 """su3_mult_host, the entry point for a and c in host memory, on both of its paths.
 
-DIRECT: a and c in pinned, mapped host memory are streamed by the kernel itself over the host
-link. STAGED: chunks are copied through HBM. Both must give, bit for bit, what su3_mult gives on
+DIRECT: a and c in pinned, mapped host memory (and, on a device that reads pageable host memory
+coherently, ordinary pageable memory) are streamed by the kernel itself over the host link. STAGED: chunks are copied through HBM. Both must give, bit for bit, what su3_mult gives on
 device copies of the same data (the same per-link operations), for every arithmetic, repr pair and
 site stride, in place too; the path taken is reported, and pad bytes of padded sites in c are
 never written."""
@@ -82,8 +82,10 @@ def test_host_paths_match_device(h, form, path):
 
 
 def test_direct_in_place_and_pageable(h):
-    """In place on pinned memory takes the direct path; pageable numpy arrays take the staged path;
-    forcing the direct path on pageable memory is refused before anything runs."""
+    """In place on pinned memory takes the direct path. Pageable numpy arrays take the direct path
+    on a device with coherent pageable access and the staged path elsewhere (the same bits either
+    way); forcing the direct path on pageable memory is refused before anything runs where the
+    device cannot read it."""
     import torch
     V = 9001
     a64, b = gen.lattice(32, V)
@@ -94,18 +96,54 @@ def test_direct_in_place_and_pageable(h):
     assert h.last_host_path() == su3.HOST_DIRECT
     assert oracle.error(pin.numpy(), ref)[0] <= 1e-13
     page = a64.copy()
-    out = np.empty_like(page)
+    out = np.full_like(page, np.nan)
     h.mult_host(d, page, b, d, out)
-    assert h.last_host_path() == su3.HOST_STAGED
+    assert h.last_host_path() == (su3.HOST_DIRECT if h.pageable_host_access() else su3.HOST_STAGED)
     assert np.array_equal(out, pin.numpy())
-    h.set_host_path(su3.HOST_DIRECT)
-    try:
-        with pytest.raises(su3.Su3Error):
-            h.mult_host(d, page, b, d, out)
-    finally:
-        h.set_host_path(su3.HOST_AUTO)
+    for path in (su3.HOST_STAGED, su3.HOST_DIRECT):
+        out2 = np.full_like(page, np.nan)
+        h.set_host_path(path)
+        try:
+            if path == su3.HOST_DIRECT and not h.pageable_host_access():
+                with pytest.raises(su3.Su3Error):
+                    h.mult_host(d, page, b, d, out2)
+                continue
+            h.mult_host(d, page, b, d, out2)
+            assert h.last_host_path() == path
+            assert np.array_equal(out2, pin.numpy())
+        finally:
+            h.set_host_path(su3.HOST_AUTO)
     with pytest.raises(su3.Su3Error):
         h.set_host_path(7)
+
+
+@pytest.mark.parametrize("form", FORMS, ids=lambda f: "dt%d-r%d%d-ar%d-s%d" % f)
+def test_pageable_direct_matches_device(h, form):
+    """Ordinary (pageable) numpy buffers on a device that reads them coherently: AUTO takes the
+    direct path, the kernel streams them as it streams pinned ones, so c has su3_mult's bits and
+    pad bytes stay untouched; in place too."""
+    if not h.pageable_host_access():
+        pytest.skip("this device does not read pageable host memory coherently")
+    dt, ri, ro, ar, stride = form
+    V = 20000 + 7
+    a64, b = gen.lattice(33, V)
+    da = su3.Desc(dt, ri, su3.AOS, V, stride, ar)
+    dc = su3.Desc(dt, ro, su3.AOS, V, stride, ar)
+    a_bytes = _packed_host(h, a64, da)
+    want = _device_result(h, da, dc, a_bytes, b)
+    a_page = a_bytes.copy()
+    c_page = np.full(su3.array_bytes(dc), 0xA5, dtype=np.uint8)
+    h.mult_host(da, a_page, b, dc, c_page)
+    assert h.last_host_path() == su3.HOST_DIRECT
+    assert np.array_equal(c_page, want)
+    assert np.array_equal(a_page, a_bytes)  # a is only read
+    if ri == ro:
+        h.mult_host(da, a_page, b, dc, a_page)  # in place: links replaced, a's pad bytes kept
+        assert h.last_host_path() == su3.HOST_DIRECT
+        exp = want.copy()
+        if stride:
+            exp.reshape(V, stride)[:, 576:] = a_bytes.reshape(V, stride)[:, 576:]
+        assert np.array_equal(a_page, exp)
 
 
 def test_direct_large_lattice_vs_oracle(h):
