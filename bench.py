@@ -741,7 +741,11 @@ def e2e_leg(h, torch, su3, a_host, b, V, args, stream, world, dev, a_dev=None, c
     out["staged_path_GBps"] = round(1152.0 * sites_all * 2 / sel / 1e9, 2)
     # ordinary pageable a and c (no pinning): on a device that reads pageable host memory
     # coherently through the host's page tables, the default path streams them as they stand; the
-    # pages are touched on the host first, as an application's own arrays would be
+    # pages are touched on the host first, as an application's own arrays would be (single-GPU
+    # runs only: at N > 1 the ranks' extra host copies would add up to hundreds of GB)
+    if world > 1:
+        del c_host
+        return out
     a_page = a_host.numpy().copy()
     c_page = np.zeros_like(a_page)
     h.mult_host(d64, a_page, b, d64, c_page, stream)  # warm
