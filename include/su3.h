@@ -189,11 +189,11 @@ su3_status su3_mat_vec(su3_handle* h, int32_t adjoint, const su3_desc* a_desc, c
  *    through the host's page tables, as on GB300 over NVLink-C2C), ordinary pageable memory
  *    (malloc, numpy) qualifies too: the kernel reads and writes it as it stands. Pages that the
  *    host never touched are first populated by the operating system, slowly, on either path.
- *  - STAGED: otherwise (pageable memory on other devices), a_host is copied to the device in chunks, multiplied
- *    and copied back into c_host, copies and kernels overlapped on the handle's streams. This
- *    allocates device staging buffers owned by the handle (three buffers of ~64 MB of input each)
- *    on the first call and whenever a larger site stride needs more; growing them synchronises
- *    the device before freeing the old ones.
+ *  - STAGED: otherwise (pageable memory on other devices), a_host is copied to the device in
+ *    chunks, multiplied and copied back into c_host, copies and kernels overlapped on the
+ *    handle's streams. This allocates device staging buffers owned by the handle (three buffers
+ *    of ~64 MB of input each) on the first call and whenever a larger site stride needs more;
+ *    growing them synchronises the device before freeing the old ones.
  * su3_set_host_path chooses between them; su3_last_host_path reports which one the last call took.
  * AOS layout only. Any arith, repr pair and site stride that su3_mult supports.
  */
