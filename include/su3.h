@@ -126,11 +126,11 @@ typedef struct {
 
 /* ---- lifetime ---------------------------------------------------------------------------- */
 
-/* Binds a new handle to CUDA device `device` (which becomes current on this thread). The
- * handle owns a small status word in device memory and the batched workspace. Later calls on the
- * handle launch on the calling thread's current device, which must be the handle's device; the
- * pointers and streams passed in must belong to it too. A handle is not thread-safe: use one per
- * host thread. */
+/* Binds a new handle to CUDA device `device`. The handle owns a small status word in device
+ * memory and the batched workspace. Every call on the handle runs on the handle's device,
+ * whichever device is current, and leaves the calling thread's current device as it was
+ * (su3_init too); the pointers and streams passed in must belong to the handle's device. A handle
+ * is not thread-safe: use one per host thread. */
 su3_status su3_init(int device, su3_handle** out);
 
 /* Releases everything the handle owns (after synchronising its device). NULL is a no-op. */
@@ -241,9 +241,9 @@ su3_status su3_mult_batched(su3_handle* h, int32_t n, const su3_batch_item* item
  *  - Runs on the calling thread's current CUDA device. The first call on each device looks up the
  *    area's device address (set-up, once per device); make that first call before any stream
  *    capture.
- *  - Items follow su3_mult_batched's rules (F64 or F32, FULL18, packed AOS, NATIVE or F64 F32PAIR; a_dev/c_dev
- *    caller-owned device buffers). More than SU3_STATIC_MAX_LATTICES non-empty items returns
- *    SU3_ERR_INVALID_ARG before anything is enqueued.
+ *  - Items follow su3_mult_batched's rules (F64 or F32, FULL18, packed AOS, NATIVE or F64
+ *    F32PAIR; a_dev/c_dev caller-owned device buffers). More than SU3_STATIC_MAX_LATTICES
+ *    non-empty items returns SU3_ERR_INVALID_ARG before anything is enqueued.
  *  - Synchronous: enqueues the descriptor upload and one kernel on `stream`, waits for `stream`,
  *    and returns SU3_ERR_TIMEOUT if a device-side bounded wait ran out (the status word at the
  *    start of the area, cleared at every call), SU3_ERR_CUDA on a CUDA error.

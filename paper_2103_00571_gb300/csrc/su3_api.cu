@@ -40,6 +40,21 @@ struct NvtxRange {
   NvtxRange& operator=(const NvtxRange&) = delete;
 };
 
+// Runs one entry point on the handle's device and gives the calling thread its current device
+// back afterwards (a no-op when the handle's device is already current).
+struct DeviceScope {
+  int prev = -1;
+  explicit DeviceScope(int dev) {
+    int cur = -1;
+    if (cudaGetDevice(&cur) == cudaSuccess && cur != dev && cudaSetDevice(dev) == cudaSuccess) prev = cur;
+  }
+  ~DeviceScope() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+  DeviceScope(const DeviceScope&) = delete;
+  DeviceScope& operator=(const DeviceScope&) = delete;
+};
+
 enum FaultPoint { kFaultNone = 0, kFaultLaunch = 1, kFaultAlloc = 2, kFaultCopy = 4, kFaultSync = 8 };
 
 int parse_fault_env() {
@@ -264,6 +279,8 @@ su3_status su3_init(int device, su3_handle** out) {
     delete h;
     return SU3_ERR_FAULT_INJECTED;
   }
+  int prev = -1;
+  if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
   cudaError_t e = cudaSetDevice(device);
   if (e == cudaSuccess) e = cudaDeviceGetAttribute(&h->num_sms, cudaDevAttrMultiProcessorCount, device);
   if (e == cudaSuccess)
@@ -280,15 +297,17 @@ su3_status su3_init(int device, su3_handle** out) {
   if (e != cudaSuccess) {
     if (h->status_dev) cudaFree(h->status_dev);
     delete h;
-    return SU3_ERR_CUDA;
+    cudaGetLastError();
+  } else {
+    *out = h;
   }
-  *out = h;
-  return SU3_OK;
+  if (prev >= 0 && prev != device) cudaSetDevice(prev);
+  return e == cudaSuccess ? SU3_OK : SU3_ERR_CUDA;
 }
 
 su3_status su3_finalize(su3_handle* h) {
   if (!h) return SU3_OK;
-  cudaSetDevice(h->device);
+  DeviceScope scope(h->device);
   cudaDeviceSynchronize();
   if (h->gexec) cudaGraphExecDestroy(h->gexec);
   if (h->cap_stream) cudaStreamDestroy(h->cap_stream);
@@ -425,6 +444,7 @@ su3_status su3_mult(su3_handle* h, const su3_desc* a_desc, const void* a_dev, co
                     const su3_desc* c_desc, void* c_dev, void* stream) {
   NvtxRange nvtx_range("su3_mult");
   if (!h) return SU3_ERR_NOT_INITIALIZED;
+  DeviceScope scope(h->device);
   if (!a_desc || !b) return fail(h, SU3_ERR_INVALID_ARG, "null descriptor or b");
   if (!c_desc) c_desc = a_desc;
   Form f;
@@ -451,6 +471,7 @@ su3_status su3_mult_op(su3_handle* h, int32_t op, const su3_desc* a_desc, const 
                        const su3_desc* c_desc, void* c_dev, void* stream) {
   NvtxRange nvtx_range("su3_mult_op");
   if (!h) return SU3_ERR_NOT_INITIALIZED;
+  DeviceScope scope(h->device);
   if (op == SU3_OP_NN) return su3_mult(h, a_desc, a_dev, b, c_desc, c_dev, stream);
   if (!b) return fail(h, SU3_ERR_INVALID_ARG, "null b");
   if (op == SU3_OP_NA) {
@@ -493,6 +514,7 @@ su3_status su3_mat_vec(su3_handle* h, int32_t adjoint, const su3_desc* a_desc, c
                        void* w_dev, void* stream) {
   NvtxRange nvtx_range("su3_mat_vec");
   if (!h) return SU3_ERR_NOT_INITIALIZED;
+  DeviceScope scope(h->device);
   if (!a_desc || !v) return fail(h, SU3_ERR_INVALID_ARG, "null descriptor or v");
   Form f;
   su3_status s = make_form(h, a_desc, a_desc, &f);
@@ -520,6 +542,7 @@ su3_status su3_mat_vec(su3_handle* h, int32_t adjoint, const su3_desc* a_desc, c
 su3_status su3_pack(su3_handle* h, const double* src, const su3_desc* dst, void* dst_dev, void* stream) {
   NvtxRange nvtx_range("su3_pack");
   if (!h) return SU3_ERR_NOT_INITIALIZED;
+  DeviceScope scope(h->device);
   if (!dst || su3_check_desc(dst) != SU3_OK) return fail(h, SU3_ERR_INVALID_ARG, "invalid destination descriptor");
   if (dst->n_sites == 0) return SU3_OK;
   if (!src || !dst_dev || !aligned16(src) || !aligned16(dst_dev))
@@ -539,6 +562,7 @@ su3_status su3_pack(su3_handle* h, const double* src, const su3_desc* dst, void*
 su3_status su3_unpack(su3_handle* h, const su3_desc* src, const void* src_dev, double* dst, void* stream) {
   NvtxRange nvtx_range("su3_unpack");
   if (!h) return SU3_ERR_NOT_INITIALIZED;
+  DeviceScope scope(h->device);
   if (!src || su3_check_desc(src) != SU3_OK) return fail(h, SU3_ERR_INVALID_ARG, "invalid source descriptor");
   if (src->n_sites == 0) return SU3_OK;
   if (!src_dev || !dst || !aligned16(src_dev) || !aligned16(dst))
@@ -558,6 +582,7 @@ su3_status su3_unpack(su3_handle* h, const su3_desc* src, const void* src_dev, d
 su3_status su3_sync(su3_handle* h, void* stream, int32_t timeout_ms) {
   NvtxRange nvtx_range("su3_sync");
   if (!h) return SU3_ERR_NOT_INITIALIZED;
+  DeviceScope scope(h->device);
   if (h->fault & kFaultSync) return fail(h, SU3_ERR_FAULT_INJECTED, "fault injected at sync");
   cudaStream_t st = (cudaStream_t)stream;
   cudaError_t e;
@@ -589,6 +614,7 @@ su3_status su3_sync(su3_handle* h, void* stream, int32_t timeout_ms) {
 su3_status su3_measure_fp64_rate(su3_handle* h, int32_t steps, double* tflops) {
   NvtxRange nvtx_range("su3_measure_fp64_rate");
   if (!h) return SU3_ERR_NOT_INITIALIZED;
+  DeviceScope scope(h->device);
   if (!tflops || steps < 1 || steps > (1 << 24)) return fail(h, SU3_ERR_INVALID_ARG, "steps must be in [1, 2^24]");
   const int grid = h->num_sms * 8;  // 2,048 threads per SM
   double* out = nullptr;
@@ -613,6 +639,7 @@ su3_status su3_measure_fp64_rate(su3_handle* h, int32_t steps, double* tflops) {
 
 su3_status su3_selftest_wait_timeout(su3_handle* h, int32_t limit_ms, void* stream) {
   if (!h) return SU3_ERR_NOT_INITIALIZED;
+  DeviceScope scope(h->device);
   if (limit_ms < 1 || limit_ms > 2000) return fail(h, SU3_ERR_INVALID_ARG, "limit_ms must be in [1, 2000]");
   return launch_selftest_wait(limit_ms, ctx_of(h, (cudaStream_t)stream));
 }
@@ -672,6 +699,7 @@ su3_status su3_mult_host(su3_handle* h, const su3_desc* a_desc, const void* a_ho
                          const su3_desc* c_desc, void* c_host, void* stream) {
   NvtxRange nvtx_range("su3_mult_host");
   if (!h) return SU3_ERR_NOT_INITIALIZED;
+  DeviceScope scope(h->device);
   if (!a_desc || !b) return fail(h, SU3_ERR_INVALID_ARG, "null descriptor or b");
   if (!c_desc) c_desc = a_desc;
   Form f;
@@ -849,6 +877,7 @@ static su3_status ensure_batch_buffers(su3_handle* h, int n, bool graph) {
 su3_status su3_mult_batched(su3_handle* h, int32_t n, const su3_batch_item* items, void* stream, int32_t use_graph) {
   NvtxRange nvtx_range("su3_mult_batched");
   if (!h) return SU3_ERR_NOT_INITIALIZED;
+  DeviceScope scope(h->device);
   if (n < 0 || (n > 0 && !items)) return fail(h, SU3_ERR_INVALID_ARG, "bad item count or null items");
   if (n == 0) return SU3_OK;
   if (h->fault & kFaultLaunch) return fail(h, SU3_ERR_FAULT_INJECTED, "fault injected at launch");
