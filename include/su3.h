@@ -189,6 +189,7 @@ su3_status su3_mat_vec(su3_handle* h, int32_t adjoint, const su3_desc* a_desc, c
  *    through the host's page tables, as on GB300 over NVLink-C2C), ordinary pageable memory
  *    (malloc, numpy) qualifies too: the kernel reads and writes it as it stands. Pages that the
  *    host never touched are first populated by the operating system, slowly, on either path.
+ *    The kernel moves 16-byte words, so both buffers must be 16-byte aligned for this path.
  *  - STAGED: otherwise (pageable memory on other devices), a_host is copied to the device in
  *    chunks, multiplied and copied back into c_host, copies and kernels overlapped on the
  *    handle's streams. This allocates device staging buffers owned by the handle (three buffers

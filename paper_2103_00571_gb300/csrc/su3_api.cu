@@ -727,7 +727,9 @@ su3_status su3_mult_host(su3_handle* h, const su3_desc* a_desc, const void* a_ho
       if (!a_view) a_view = pageable_view(a_host);
       if (!c_view) c_view = pageable_view(c_host);
     }
-    if (a_view && c_view) {
+    // the kernel moves 16-byte words: other buffers take the staged path (copies of any alignment)
+    const bool aligned = aligned16(a_host) && aligned16(c_host) && aligned16(a_view) && aligned16(c_view);
+    if (a_view && c_view && aligned) {
       h->host_path_used = SU3_HOST_DIRECT;
       s = launch_mult_host_direct(f, cfg, a_view, b, c_view, ctx_of(h, user));
       if (s != SU3_OK) return s;
@@ -735,7 +737,8 @@ su3_status su3_mult_host(su3_handle* h, const su3_desc* a_desc, const void* a_ho
     }
     if (h->host_path == SU3_HOST_DIRECT)
       return fail(h, SU3_ERR_INVALID_ARG,
-                  h->pageable_access
+                  !aligned ? "the direct host path needs 16-byte aligned a and c"
+                  : h->pageable_access
                       ? "the direct host path needs a and c in host memory (pinned, mapped or pageable)"
                       : "the direct host path needs a and c each inside one pinned, mapped host allocation "
                         "(this device does not read pageable host memory)");

@@ -146,6 +146,43 @@ def test_pageable_direct_matches_device(h, form):
         assert np.array_equal(a_page, exp)
 
 
+def test_misaligned_host_buffers_take_the_staged_path(h):
+    """The kernel streams 16-byte words, so buffers that are not 16-byte aligned (pinned or
+    pageable) are copied through HBM under AUTO, with the same bits; a forced direct path is
+    refused before anything runs."""
+    import torch
+    V = 3001
+    n = V * 72
+    a64, b = gen.lattice(34, V)
+    d = su3.Desc(su3.F64, su3.FULL18, su3.AOS, V)
+    a_al = torch.from_numpy(a64.copy()).pin_memory()
+    c_al = torch.empty(n, dtype=torch.float64).pin_memory()
+    h.mult_host(d, a_al.data_ptr(), b, d, c_al.data_ptr())
+    assert h.last_host_path() == su3.HOST_DIRECT
+    want = c_al.numpy().copy()
+    pa = torch.zeros(n + 2, dtype=torch.float64).pin_memory()
+    pc = torch.zeros(n + 2, dtype=torch.float64).pin_memory()
+    pa.numpy()[1:1 + n] = a64
+    h.mult_host(d, pa.data_ptr() + 8, b, d, pc.data_ptr() + 8)  # both 8 bytes off a 16-byte boundary
+    assert h.last_host_path() == su3.HOST_STAGED
+    assert np.array_equal(pc.numpy()[1:1 + n], want)
+    page_a = np.zeros(n + 2)
+    page_a[1:1 + n] = a64
+    page_c = np.zeros(n + 2)
+    a_view, c_view = page_a[1:1 + n], page_c[1:1 + n]
+    assert a_view.ctypes.data % 16 == 8
+    h.mult_host(d, a_view, b, d, c_view)
+    assert h.last_host_path() == su3.HOST_STAGED
+    assert np.array_equal(c_view, want)
+    h.set_host_path(su3.HOST_DIRECT)
+    try:
+        for args in ((pa.data_ptr() + 8, pc.data_ptr() + 8), (a_view, c_view), (a_al.data_ptr(), pc.data_ptr() + 8)):
+            with pytest.raises(su3.Su3Error):
+                h.mult_host(d, args[0], b, d, args[1])
+    finally:
+        h.set_host_path(su3.HOST_AUTO)
+
+
 def test_direct_large_lattice_vs_oracle(h):
     """A lattice far larger than L2 (L=40, 1.47 GB each way) through the direct path, checked
     against the oracle on a sample of sites spread over the whole lattice."""
