@@ -525,8 +525,39 @@ def run_native(args, world, rank, local):
     elif rank == 0:
         line["e2e"] = None
     if rank == 0:
+        line["summary"] = summary(line)  # last key: the compact digest ends the line
         print(json.dumps(line), flush=True)
     h.close()
+
+
+def summary(line):
+    """The line's key figures in a few hundred bytes: the headline with both roofline fractions,
+    the fastest FP64-accurate form, every form as [GB/s, G site/s, max error, within tolerance],
+    the batch and the end-to-end path."""
+    rf = line["roofline"]
+    out = {"headline": {"form": line["config"]["form"], "GBps": line["value"],
+                        "Gsite_per_s": round(line["site_updates_per_s"] / 1e9, 3),
+                        "frac": rf["frac"], "bound": rf["bound"],
+                        "hbm_frac": rf.get("hbm", {}).get("frac", rf["frac"] if rf["bound"] == "hbm" else None)}}
+    fa = line.get("fp64_accurate")
+    if fa:
+        out["fp64_accurate"] = {"form": fa["form"], "GBps": fa["GBps"], "hbm_frac": fa["roofline"]["frac"],
+                                "max_err": float("%.3g" % fa["max_err"]), "tol": fa["tol"], "ok": fa["ok"]}
+    if "forms" in line:
+        out["forms"] = {n: [f["GBps"], round(f["site_updates_per_s"] / 1e9, 3), float("%.2g" % f["max_err"]),
+                            f["ok"]] for n, f in line["forms"].items()}
+    bt = line.get("batched")
+    if bt:
+        out["batched"] = {n: [bt[n]["ms"], round(bt[n]["site_updates_per_s"] / 1e9, 3), bt[n]["ok"]]
+                          for n in ("graph_persistent", "graph_persistent_f64_as_f32pair", "per_lattice_loop")
+                          if n in bt}
+    e2e = line.get("e2e")
+    if e2e:
+        out["e2e"] = {"GBps": e2e["value"], "path": e2e.get("path"), "vs_copies_only": e2e.get("vs_copies_only")}
+    cpu = line.get("cpu_baseline")
+    if cpu:
+        out["cpu_oracle_GBps"] = cpu["value"]
+    return out
 
 
 def sample_error(torch, c_dev_f64, ref, V_sample):

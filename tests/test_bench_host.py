@@ -88,3 +88,23 @@ def test_form_names_round_trip():
     assert any(tune.is_pair_name(n) for n in tune.ALL_FORMS)
     d = tune.parse_form("f64-full-aos-f32pair-p640")
     assert (d.site_stride_bytes, d.arith) == (640, su3.F32PAIR) and tune.form_name(d) == "f64-full-aos-f32pair-p640"
+
+
+def test_summary_ends_the_line_and_stays_short():
+    """The compact digest holds the headline, the FP64-accurate form, every form, the batch and the
+    end-to-end figure, and fits in the last kilobyte and a half of the printed line."""
+    form = {"GBps": 5963.1, "site_updates_per_s": 5.18e9, "max_err": 3.3e-14, "ok": True}
+    line = {"value": 1589.2, "site_updates_per_s": 1.38e9, "config": {"form": "f64-full18-aos-native"},
+            "roofline": {"bound": "alu", "frac": 0.947, "hbm": {"frac": 0.239}},
+            "fp64_accurate": {"form": "f64-f32pair-aos", "GBps": 5963.1, "max_err": 3.3e-14, "tol": 1e-13,
+                              "ok": True, "roofline": {"frac": 0.8956}},
+            "forms": {name: dict(form) for name, *_ in bench.FORMS},
+            "batched": {k: {"ms": 1.27, "site_updates_per_s": 2.34e9, "ok": True}
+                        for k in ("graph_persistent", "graph_persistent_f64_as_f32pair", "per_lattice_loop")},
+            "e2e": {"value": 333.1, "path": "direct", "vs_copies_only": 1.9}, "cpu_baseline": {"value": 31.1}}
+    s = bench.summary(line)
+    assert s["headline"]["hbm_frac"] == 0.239 and s["fp64_accurate"]["hbm_frac"] == 0.8956
+    assert set(s["forms"]) == {name for name, *_ in bench.FORMS}
+    assert s["forms"]["f64-f32pair-aos"] == [5963.1, 5.18, 3.3e-14, True]
+    assert s["e2e"]["GBps"] == 333.1 and s["batched"]["graph_persistent"][2] is True
+    assert len(json.dumps({"summary": s})) < 1400
