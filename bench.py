@@ -56,6 +56,9 @@ def parse():
                     help="arithmetic of the FP64 AoS step (native = the plain FP64 method)")
     ap.add_argument("--dtype", default="f64", choices=["f64", "f32", "f16", "bf16"],
                     help="storage type of the timed step (other than f64: with --quick, for profiling)")
+    ap.add_argument("--stride", type=int, default=0,
+                    help="AoS site stride in bytes of the timed step's a and c, wider than the links "
+                         "(640: the paper's padded FP64 Site); with --quick, for profiling")
     ap.add_argument("--shard", action="store_true",
                     help="N > 1: split one lattice into contiguous slabs of sites, one per rank (strong "
                          "scaling) instead of one lattice per rank (replicas, weak scaling)")
@@ -340,7 +343,7 @@ def traffic_record():
 
 
 # the sources that define the single-lattice AoS kernels (the ones the traffic records describe)
-AOS_KERNEL_SOURCES = ("su3_device.cuh", "su3_internal.h", "su3_stream.cu")
+AOS_KERNEL_SOURCES = ("su3_device.cuh", "su3_internal.h", "su3_stream.cuh", "su3_stream.cu", "su3_stream_padded.cu")
 
 
 def source_digest():
@@ -397,11 +400,11 @@ def run_native(args, world, rank, local):
     c_dev = torch.empty_like(a_dev)
     arith = {"native": su3.NATIVE, "f32pair": su3.F32PAIR, "hybrid": su3.HYBRID}[args.arith]
     dt = {"f64": su3.F64, "f32": su3.F32, "f16": su3.F16, "bf16": su3.BF16}[args.dtype]
-    if dt != su3.F64 and not args.quick:
-        raise SystemExit("--dtype other than f64 times the reduced form alone: use it with --quick")
-    d64 = su3.Desc(dt, su3.FULL18, su3.AOS, V, 0, arith if dt == su3.F64 else su3.NATIVE)
+    if (dt != su3.F64 or args.stride) and not args.quick:
+        raise SystemExit("--dtype other than f64 and --stride time that form alone: use them with --quick")
+    d64 = su3.Desc(dt, su3.FULL18, su3.AOS, V, args.stride, arith if dt == su3.F64 else su3.NATIVE)
     a_step, c_step = a_dev, c_dev
-    if dt != su3.F64:
+    if dt != su3.F64 or args.stride:
         a_step = torch.empty(su3.array_bytes(d64), dtype=torch.uint8, device=dev)
         c_step = torch.empty_like(a_step)
         h.pack(a_dev, d64, a_step, stream)
@@ -438,21 +441,23 @@ def run_native(args, world, rank, local):
         fp64_measured = h.measure_fp64_rate(8192)
     except su3.Su3Error:
         fp64_measured = None
-    tr = traffic_record().get("su3_aos_kernel<f64,full>", {})
+    pad = ",p%d" % args.stride if args.stride else ""  # padded sites: the kernel of their own
+    padded = "true" if args.stride else "false"
+    tr = traffic_record().get("su3_aos_kernel<f64,full%s>" % pad, {})
     traffic = None
     if tr and tr.get("source_digest") == source_digest():
         traffic = tr["bytes_per_site"] * V
     hbm_roof = {"achieved": round(achieved_gbs, 1), "peak": hbm_peak, "unit": "GB/s",
                 "frac": round(achieved_gbs / hbm_peak, 4), "peak_source": peak_src + " hbm_gbs"}
     if dt != su3.F64:
-        tr = traffic_record().get("su3_aos_kernel<%s,full>" % args.dtype, {})
+        tr = traffic_record().get("su3_aos_kernel<%s,full%s>" % (args.dtype, pad), {})
         traffic = tr["bytes_per_site"] * V if tr and tr.get("source_digest") == source_digest() else None
         roofline = dict(hbm_roof, bound="hbm", traffic=traffic,
-                        kernel="su3_aos_kernel<NativeOp<%s,9,3>, %d, AOS>" % (args.dtype.upper(), tpl))
+                        kernel="su3_aos_kernel<NativeOp<%s,9,3>, %d, AOS, %s>" % (args.dtype.upper(), tpl, padded))
     elif args.arith == "native":
         roofline = {"bound": "alu", "achieved": round(achieved_tf, 4), "peak": round(fp64_peak, 4),
                     "unit": "TFLOP/s", "frac": round(achieved_tf / fp64_peak, 4), "traffic": traffic,
-                    "kernel": "su3_aos_kernel<NativeOp<F64,9,3>, %d, AOS>" % tpl,
+                    "kernel": "su3_aos_kernel<NativeOp<F64,9,3>, %d, AOS, %s>" % (tpl, padded),
                     "peak_source": "FP64 pipe: %d SMs (this device) x 2 DFMA/clk x 2 flop x %.0f MHz (max SM clock)"
                                        % (sms, sm_max),
                     "peak_measured": round(fp64_measured, 4) if fp64_measured else None,
@@ -461,11 +466,11 @@ def run_native(args, world, rank, local):
                                             "2,048 threads per SM, CUDA events",
                     "hbm": hbm_roof}
     else:
-        tr = traffic_record().get("su3_aos_kernel<f64,full,%s>" % args.arith, {})
+        tr = traffic_record().get("su3_aos_kernel<f64,full,%s%s>" % (args.arith, pad), {})
         traffic = tr["bytes_per_site"] * V if tr and tr.get("source_digest") == source_digest() else None
         roofline = dict(hbm_roof, bound="hbm", traffic=traffic,
-                        kernel="su3_aos_kernel<%s<9,3>, %d, AOS>" % ("PairF64Op" if args.arith == "f32pair" else "HybridF64Op",
-                                                                        tpl))
+                        kernel="su3_aos_kernel<%s<9,3>, %d, AOS, %s>" % ("PairF64Op" if args.arith == "f32pair" else "HybridF64Op",
+                                                                            tpl, padded))
 
     line = {"metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": round(total_ms / args.steps, 4), "higher_is_better": True,
@@ -474,11 +479,14 @@ def run_native(args, world, rank, local):
                       if dt == su3.F64 else "%s storage, f32 math" % args.dtype),
             "data": "synthetic",
             "config": {"workload": "L=%d %s AoS SU3_Bench link multiply (c[i][j] = a[i][j] x b[j], "
-                                   "%d sites, %d B read + %d B written per site)%s"
+                                   "%d sites, %d B read + %d B written per site)%s%s"
                                    % (L, args.dtype.upper(), V_lattice, bytes_per_step / V / 2, bytes_per_step / V / 2,
-                                      ", split into %d slabs of contiguous sites" % world if args.shard else ""),
+                                      ", split into %d slabs of contiguous sites" % world if args.shard else "",
+                                      ", sites padded to %d B (links only are read and written)" % args.stride
+                                      if args.stride else ""),
                        "lattice": "%d^4" % L,
-                       "form": ("f64-full18-aos-" + args.arith) if dt == su3.F64 else args.dtype + "-full18-aos",
+                       "form": (("f64-full18-aos-" + args.arith) if dt == su3.F64 else args.dtype + "-full18-aos")
+                               + ("-p%d" % args.stride if args.stride else ""),
                        "seed": SEED,
                        "inputs": "random SU(3) (Gram-Schmidt on Gaussian rows), one lattice per GPU",
                        "l2": "inputs larger than L2 (%.1f GB touched per step vs 129 MB L2): no flush"
@@ -517,7 +525,7 @@ def run_native(args, world, rank, local):
                 "roofline": {"bound": "hbm", "achieved": fa["GBps"], "peak": hbm_peak, "unit": "GB/s",
                              "frac": round(fa["GBps"] / hbm_peak, 4), "peak_source": peak_src + " hbm_gbs",
                              "traffic": tr["bytes_per_site"] * V if tr and tr.get("source_digest") == source_digest() else None,
-                             "kernel": "su3_aos_kernel<PairF64Op<9,3>, 1, AOS>"}}
+                             "kernel": "su3_aos_kernel<PairF64Op<9,3>, 1, AOS, false>"}}
     if not args.quick:
         line["e2e"] = e2e_leg(h, torch, su3, a_host, b, V, args, stream, world, dev, a_dev, c_dev, sites_all)
         if world == 1:
@@ -531,9 +539,9 @@ def run_native(args, world, rank, local):
 
 
 def summary(line):
-    """The line's key figures in a few hundred bytes: the headline with both roofline fractions,
-    the fastest FP64-accurate form, every form as [GB/s, G site/s, max error, within tolerance],
-    the batch and the end-to-end path."""
+    """The line's key figures in about 1.3 kB: the headline with both roofline fractions, the
+    fastest FP64-accurate form, every form as [GB/s, G site/s, max error] and whether all are
+    within their tolerances, the paper's 640-byte Site, the batch and the end-to-end path."""
     rf = line["roofline"]
     out = {"headline": {"form": line["config"]["form"], "GBps": line["value"],
                         "Gsite_per_s": round(line["site_updates_per_s"] / 1e9, 3),
@@ -544,8 +552,12 @@ def summary(line):
         out["fp64_accurate"] = {"form": fa["form"], "GBps": fa["GBps"], "hbm_frac": fa["roofline"]["frac"],
                                 "max_err": float("%.3g" % fa["max_err"]), "tol": fa["tol"], "ok": fa["ok"]}
     if "forms" in line:
-        out["forms"] = {n: [f["GBps"], round(f["site_updates_per_s"] / 1e9, 3), float("%.2g" % f["max_err"]),
-                            f["ok"]] for n, f in line["forms"].items()}
+        out["forms"] = {n: [round(f["GBps"]), round(f["site_updates_per_s"] / 1e9, 2), float("%.2g" % f["max_err"])]
+                        for n, f in line["forms"].items()}
+        out["forms_within_tol"] = all(f["ok"] for f in line["forms"].values())
+    p640 = line.get("paper_site640")
+    if p640:
+        out["site640_Gsite_per_s"] = {k: round(v["site_updates_per_s"] / 1e9, 2) for k, v in p640.items()}
     bt = line.get("batched")
     if bt:
         out["batched"] = {n: [bt[n]["ms"], round(bt[n]["site_updates_per_s"] / 1e9, 3), bt[n]["ok"]]
@@ -616,7 +628,7 @@ def forms_leg(h, torch, su3, a_dev, b, V, stream, f64_gbs, ref, V_sample, reps=1
 def site640_leg(h, torch, su3, a_dev, b, V, stream, ref, V_sample, reps=10):
     """The paper's own FP64 Site: 4 links plus coordinates, index, parity and padding to 640 bytes
     (§Background), so a site update moves 2 x 640 B by the paper's accounting while the kernel
-    reads 640 B (pads included, in whole bulk copies) and writes only the 576 link bytes per site."""
+    reads and writes only the 576 link bytes of each site (2-D tensor copies of whole tiles)."""
     d = su3.Desc(su3.F64, su3.FULL18, su3.AOS, V, 640)
     abuf = torch.empty(su3.array_bytes(d), dtype=torch.uint8, device=a_dev.device)
     cbuf = torch.zeros_like(abuf)

@@ -12,7 +12,7 @@ CSRC = os.path.join(PKG, "csrc")
 INCLUDE = os.path.join(ROOT, "include")
 OUT_DIR = os.path.join(PKG, "_lib")
 LIB = os.path.join(OUT_DIR, "libsu3.so")
-SOURCES = ["su3_api.cu", "su3_stream.cu", "su3_host.cu", "su3_pack.cu", "su3_batched.cu", "su3_diag.cu"]
+SOURCES = ["su3_api.cu", "su3_stream.cu", "su3_stream_padded.cu", "su3_host.cu", "su3_pack.cu", "su3_batched.cu", "su3_diag.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 
 

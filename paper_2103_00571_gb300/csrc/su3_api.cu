@@ -135,8 +135,8 @@ LaunchCtx ctx_of(su3_handle* h, cudaStream_t st) {
 }
 
 // Launch configurations are kept per (dtype, repr of a, repr of c, layout, arith, padded): an AOS
-// site stride wider than the links (the paper's 640-byte FP64 site) needs more shared memory per
-// site and gets its own configuration, and so does two-row in, full out (its kernel also keeps an
+// site stride wider than the links (the paper's 640-byte FP64 site) moves each site's links in
+// bulk copies of their own and gets its own configuration, and so does two-row in, full out (its kernel also keeps an
 // output ring and, in FP32 pairs, needs more registers than two-row in and out).
 using CfgKey = std::tuple<int, int, int, int, int, int>;
 CfgKey form_key(const su3_desc* d, int repr_out) {

@@ -80,6 +80,27 @@ __device__ __forceinline__ void bulk_s2g(void* gdst, const void* ssrc, unsigned 
                : "memory");
 }
 
+// 2-D tensor copies (the TMA engine reading a tensor map): the box at element coordinates (x, y)
+// of the map. Load: global -> this CTA's shared memory, completing the box's bytes on `bar` (rows
+// past the tensor's end arrive as zeros and count like the rest). Store: shared -> global, tracked
+// by this thread's bulk groups; rows past the tensor's end are not written. The map is a
+// __grid_constant__ kernel parameter (its generic address); shared memory 128-byte aligned.
+__device__ __forceinline__ void tma_load_2d(void* sdst, const void* tmap, int x, int y, uint64_t* bar,
+                                            uint64_t policy) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes.L2::cache_hint [%0], "
+      "[%1, {%2, %3}], [%4], %5;" ::"r"(smem_u32(sdst)),
+      "l"(tmap), "r"(x), "r"(y), "r"(smem_u32(bar)), "l"(policy)
+      : "memory");
+}
+
+__device__ __forceinline__ void tma_store_2d(const void* tmap, int x, int y, const void* ssrc, uint64_t policy) {
+  asm volatile("cp.async.bulk.tensor.2d.global.shared::cta.tile.bulk_group.L2::cache_hint [%0, {%1, %2}], [%3], %4;" ::"l"(
+                   tmap),
+               "r"(x), "r"(y), "r"(smem_u32(ssrc)), "l"(policy)
+               : "memory");
+}
+
 __device__ __forceinline__ void bulk_commit() { asm volatile("cp.async.bulk.commit_group;" ::: "memory"); }
 
 template <int N>

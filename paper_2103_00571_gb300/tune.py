@@ -135,7 +135,7 @@ def candidates(desc, out=None):
         return out
     rows = 3 if out.repr == B.FULL18 else 2  # output rows: threads per link under the row split
     if desc.layout == B.AOS:
-        site = desc.site_stride_bytes or B.link_bytes(desc.dtype, desc.repr) * 4
+        site = B.link_bytes(desc.dtype, desc.repr) * 4  # shared-memory tiles are packed whatever the stride
         out = []  # threads_per_link 3 = one thread per output row
         for block, stages, cps, tpl in itertools.product((64, 128, 192, 256), (3, 4, 6), (1, 2, 3), (1, 3)):
             # tiles of ~9/18/36 KB, and tiles of exactly one or two links per thread

@@ -101,10 +101,12 @@ def test_summary_ends_the_line_and_stays_short():
             "forms": {name: dict(form) for name, *_ in bench.FORMS},
             "batched": {k: {"ms": 1.27, "site_updates_per_s": 2.34e9, "ok": True}
                         for k in ("graph_persistent", "graph_persistent_f64_as_f32pair", "per_lattice_loop")},
-            "e2e": {"value": 333.1, "path": "direct", "vs_copies_only": 1.9}, "cpu_baseline": {"value": 31.1}}
+            "e2e": {"value": 333.1, "path": "direct", "vs_copies_only": 1.9}, "cpu_baseline": {"value": 31.1},
+            "paper_site640": {"native": {"site_updates_per_s": 1.38e9}, "f32pair": {"site_updates_per_s": 5.09e9}}}
     s = bench.summary(line)
     assert s["headline"]["hbm_frac"] == 0.239 and s["fp64_accurate"]["hbm_frac"] == 0.8956
     assert set(s["forms"]) == {name for name, *_ in bench.FORMS}
-    assert s["forms"]["f64-f32pair-aos"] == [5963.1, 5.18, 3.3e-14, True]
+    assert s["forms"]["f64-f32pair-aos"] == [5963, 5.18, 3.3e-14] and s["forms_within_tol"] is True
+    assert s["site640_Gsite_per_s"] == {"native": 1.38, "f32pair": 5.09}
     assert s["e2e"]["GBps"] == 333.1 and s["batched"]["graph_persistent"][2] is True
     assert len(json.dumps({"summary": s})) < 1400

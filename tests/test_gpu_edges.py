@@ -93,7 +93,8 @@ def test_stride_640_keeps_pads_and_canaries(h, arith, cfg):
                                           (su3.BF16, 208)])
 def test_generic_site_strides(h, dtype, stride):
     """Any 16-byte-multiple site stride at least the link bytes: links land at each site's start,
-    the bytes after them are left alone, for one and three threads per link."""
+    the bytes after them are left alone, for one and three threads per link, and for a tile wider
+    than the 256 sites one tensor copy moves (the launcher narrows it)."""
     import torch
     V = 3001
     a, b = gen.lattice(14, V)
@@ -108,8 +109,8 @@ def test_generic_site_strides(h, dtype, stride):
     tol = {su3.F64: 1e-13, su3.F32: 2e-6, su3.F16: 5e-3, su3.BF16: 3e-2}[dtype]
     saved = h.get_launch_cfg(d)
     try:
-        for tpl in (1, 3):
-            h.set_launch_cfg(d, block=128, tile_sites=48, stages=3, ctas_per_sm=2, threads_per_link=tpl)
+        for tiles, tpl in ((48, 1), (48, 3), (300, 1)):
+            h.set_launch_cfg(d, block=128, tile_sites=tiles, stages=3, ctas_per_sm=1, threads_per_link=tpl)
             dst = torch.full((V * stride,), 0xC3, dtype=torch.uint8, device="cuda")
             h.mult(d, src, b, d, dst)
             h.sync()
@@ -121,6 +122,49 @@ def test_generic_site_strides(h, dtype, stride):
             assert oracle.error(out.cpu().numpy(), ref)[0] <= tol, tpl
     finally:
         h.set_launch_cfg(d, **saved)
+
+
+@pytest.mark.parametrize("arith", [su3.NATIVE, su3.F32PAIR])
+@pytest.mark.parametrize("reprs", [(su3.FULL18, su3.FULL18), (su3.TWOROW12, su3.FULL18), (su3.TWOROW12, su3.TWOROW12)],
+                         ids=["full", "2row-to-full", "2row"])
+def test_mixed_site_strides_bitwise(arith, reprs):
+    """a and c with site strides of their own (padded a into packed c, packed a into padded c, two
+    different padded strides): each gives the packed-stride bits, leaves the bytes after c's links
+    alone, for one and three threads per link and tiles narrower and wider than the 32 sites one
+    warp copies per pass."""
+    import torch
+    h = su3.Handle(0)  # its own handle: the configurations below stay local to it
+    ri, ro = reprs
+    V = 2777
+    a, b = gen.lattice(15, V)
+    dpa, dpc = su3.Desc(su3.F64, ri, su3.AOS, V, 0, arith), su3.Desc(su3.F64, ro, su3.AOS, V, 0, arith)
+    la, lc = su3.array_bytes(dpa) // V, su3.array_bytes(dpc) // V  # link bytes per site
+    packed_a = empty_bytes(su3.array_bytes(dpa))
+    h.pack(to_dev(a), dpa, packed_a)
+    ref = empty_bytes(su3.array_bytes(dpc))
+    h.mult(dpa, packed_a, b, dpc, ref)
+    out = torch.empty(V * 72, dtype=torch.float64, device="cuda")
+    h.unpack(dpc, ref, out)
+    h.sync()
+    assert oracle.error(out.cpu().numpy(), oracle.mult(a, b))[0] <= (1e-13 if ri == su3.FULL18 else 1e-12)
+    ref = ref.cpu()
+    for sa, sc in ((la + 64, 0), (0, lc + 128), (la + 16, lc + 64)):
+        da, dc = su3.Desc(su3.F64, ri, su3.AOS, V, sa, arith), su3.Desc(su3.F64, ro, su3.AOS, V, sc, arith)
+        src = packed_a
+        if sa:
+            src = torch.full((V * sa,), 0x3C, dtype=torch.uint8, device="cuda")
+            src.view(V, sa)[:, :la] = packed_a.view(V, la)
+        for tiles, tpl in ((24, 1), (80, 1), (40, 3), (72, 3)):
+            h.set_launch_cfg(da, block=128, tile_sites=tiles, stages=3, ctas_per_sm=2, threads_per_link=tpl)
+            h.set_launch_cfg_for(da, dc, block=128, tile_sites=tiles, stages=3, ctas_per_sm=2, threads_per_link=tpl)
+            dst = torch.full((V * (sc or lc),), 0xC3, dtype=torch.uint8, device="cuda")
+            h.mult(da, src, b, dc, dst)
+            h.sync()
+            host = dst.view(V, sc or lc).cpu()
+            assert torch.equal(host[:, :lc].contiguous().view(-1), ref), (sa, sc, tiles, tpl)
+            if sc:
+                assert bool(torch.all(host[:, lc:] == 0xC3)), "bytes after the links were written"
+    h.close()
 
 
 def test_canaries_packed(h):
