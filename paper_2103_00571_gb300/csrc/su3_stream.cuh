@@ -101,6 +101,14 @@ __global__ void __launch_bounds__(256) su3_aos_kernel(const __grid_constant__ Ao
   using BA = typename Op::BArg;
   constexpr int NE_IN = Op::kNeIn, NE_OUT = Op::kNeOut;
   constexpr bool kInPlace = (NE_OUT == NE_IN);
+  // FP64 two-row in, full out, packed AoS sites, one thread per link: each warp stages its 32
+  // consecutive links' results (4.6 KB) in a double-buffered slot of its own and drains it with one
+  // bulk copy, instead of the CTA filling a ring of 3 whole-tile output buffers. A CTA then needs
+  // about half the shared memory, so a third one fits on an SM (FP32-pair form: 4.34 -> 4.60 G
+  // site/s at L=48). Narrower outputs keep the ring: for matrix x vector products (0.8-1.5 KB per
+  // warp copy) per-warp copies measured up to 2.3x slower; FP32/FP16 storage keeps it too.
+  constexpr bool kWarpOut = !kInPlace && LAYOUT == SU3_LAYOUT_AOS && TPL == 1 && !PADDED && NE_IN == 6 &&
+                            NE_OUT == 9 && sizeof(V) == 16;
   constexpr int kVec = (int)sizeof(V);
   constexpr int kLinkIn = NE_IN * kVec;
   constexpr int kLinkOut = NE_OUT * kVec;
@@ -176,6 +184,7 @@ __global__ void __launch_bounds__(256) su3_aos_kernel(const __grid_constant__ Ao
                                      : (p.c_stride == 4 * kLinkOut);
   int issued = my_tiles < prefetch ? my_tiles : prefetch;  // loads issued so far (thread 0's view)
   int kfail = -1;
+  int wpar = 0;  // kWarpOut: which of the warp's two output slots is next
 
   for (int k = 0; k < my_tiles; ++k) {
     const int s = k % S_;
@@ -184,7 +193,30 @@ __global__ void __launch_bounds__(256) su3_aos_kernel(const __grid_constant__ Ao
     const bool ok = mbar_wait_bounded(&full[s], (unsigned)((k / S_) & 1));
     unsigned char* in = stage0 + (size_t)s * p.stage_bytes;
     unsigned char* out = kInPlace ? in : out0 + (size_t)(k % 3) * p.out_bytes;
-    if (ok) {
+    if (ok && kWarpOut) {
+      op.begin_tile(k);
+      const int links = 4 * nt, lane = tid & 31;
+      const long long first = (long long)t * p.tile_sites;
+      for (int base = tid - lane; base < links; base += blockDim.x) {  // warp-uniform
+        unsigned char* slot = out0 + ((size_t)(tid >> 5) * 2 + wpar) * 32 * kLinkOut;
+        if (lane == 0) bulk_wait_read<1>();  // the store issued two slots back has read this slot
+        __syncwarp();
+        const int link = base + lane;
+        if (link < links) {
+          const int site = link >> 2, j = link & 3;
+          op.template apply<ES, ES>(reinterpret_cast<const V*>(in + (size_t)site * p.a_stride + j * kLinkIn),
+                                    reinterpret_cast<V*>(slot + (size_t)lane * kLinkOut));
+        }
+        fence_proxy_async_smem();
+        __syncwarp();
+        if (lane == 0) {  // links base .. base + n - 1 of the tile are contiguous in packed c
+          const int n = links - base < 32 ? links - base : 32;
+          bulk_s2g(p.c + (4 * first + base) * kLinkOut, slot, (unsigned)(n * kLinkOut), pol);
+          bulk_commit();
+        }
+        wpar ^= 1;
+      }
+    } else if (ok) {
       op.begin_tile(k);
       const int links = 4 * nt;
       for (int q = tid; q < TPL * links; q += blockDim.x) {
@@ -211,12 +243,14 @@ __global__ void __launch_bounds__(256) su3_aos_kernel(const __grid_constant__ Ao
       }
     }
     fence_proxy_async_smem();
-    if (!kInPlace && tid < 32) bulk_wait_read<1>();  // store(k-2) done reading out[(k+1)%3]
+    if (!kInPlace && !kWarpOut && tid < 32) bulk_wait_read<1>();  // store(k-2) done reading out[(k+1)%3]
     if (__syncthreads_or(!ok)) {
       kfail = k;
       break;
     }
-    if (tid < 32) {
+    if (kWarpOut) {  // the warps stored their own links; stage s has been read by all of them
+      if (tid == 0 && issued < my_tiles) issue_load(issued++);
+    } else if (tid < 32) {
       // store tile k
       const long long first = (long long)t * p.tile_sites;
       if constexpr (LAYOUT == SU3_LAYOUT_AOS) {
@@ -265,7 +299,7 @@ __global__ void __launch_bounds__(256) su3_aos_kernel(const __grid_constant__ Ao
     // let the loads still in flight land before shared memory is released (bounded)
     for (int k = kfail; k < issued; ++k) mbar_wait_bounded(&full[k % S_], (unsigned)((k / S_) & 1));
   }
-  if (tid < 32) bulk_wait_all<0>();
+  if (kWarpOut ? (tid & 31) == 0 : tid < 32) bulk_wait_all<0>();
 }
 
 // ---- SOA / AOSOA32: direct coalesced loads ----------------------------------------------------
@@ -365,7 +399,13 @@ static su3_status run_aos(const Form& f, const LaunchCfg& cfg, const void* a, co
     if (LAYOUT == SU3_LAYOUT_SOA) return r128(Op::kNeOut * kSoaPlaneLinks * kVec);
     return r128(ts * 4 * kLinkOut);
   };
-  auto smem_of = [&](long long ts) { return kSmemHeader + cfg.stages * in_bytes(ts) + 3 * out_bytes(ts); };
+  // separate outputs: two slots of 32 links per warp (the kernel's kWarpOut case), else a ring of
+  // 3 whole-tile buffers
+  const bool warp_out = !kInPlace && LAYOUT == SU3_LAYOUT_AOS && !PADDED && cfg.threads_per_link == 1 &&
+                        Op::kNeIn == 6 && Op::kNeOut == 9 && kVec == 16;
+  auto smem_of = [&](long long ts) {
+    return kSmemHeader + cfg.stages * in_bytes(ts) + (warp_out ? cfg.block / 32 * 2 * 32 * kLinkOut : 3 * out_bytes(ts));
+  };
 
   long long ts = cfg.tile_sites;
   // padded AOS sites move through tensor copies whose box holds at most 256 rows
@@ -419,7 +459,7 @@ static su3_status run_aos(const Form& f, const LaunchCfg& cfg, const void* a, co
   }
   p.n_tiles = (int)n_tiles;
   p.stage_bytes = (unsigned)in_bytes(ts);
-  p.out_bytes = (unsigned)out_bytes(ts);
+  p.out_bytes = warp_out ? 0u : (unsigned)out_bytes(ts);
   p.native_warps = native_warps(f, cfg);
   const int grid = (int)std::min<long long>(p.n_tiles, (long long)ctx.num_sms * cfg.ctas_per_sm);
   p.status = ctx.status;
