@@ -59,6 +59,9 @@ def parse():
     ap.add_argument("--stride", type=int, default=0,
                     help="AoS site stride in bytes of the timed step's a and c, wider than the links "
                          "(640: the paper's padded FP64 Site); with --quick, for profiling")
+    ap.add_argument("--form", default="",
+                    help="with --quick: time this form alone, named as the tuner names forms "
+                         "(dtype-repr-layout[-arith][-p<stride>], e.g. f64-2to18-aos-f32pair)")
     ap.add_argument("--shard", action="store_true",
                     help="N > 1: split one lattice into contiguous slabs of sites, one per rank (strong "
                          "scaling) instead of one lattice per rank (replicas, weak scaling)")
@@ -135,6 +138,16 @@ class ClockSampler:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": [], "samples": 0}
         return {"sm_mhz": statistics.median(sm), "sm_max_mhz": max(mx), "reasons": sorted(reasons),
                 "samples": len(sm)}
+
+
+def flop_per_site(repr_in, repr_out):
+    """Flops of one site update by the paper's count (8 per complex multiply-add): 864 for the
+    full product, 576 for rows 0-1 only (two-row in and out), 1056 for two-row in, full out (the
+    rebuilt row 2 of a adds 2 complex multiply-adds per element, 48 flops per link)."""
+    import paper_2103_00571_gb300 as su3
+    if repr_in == su3.FULL18:
+        return FLOP_PER_SITE
+    return 576 if repr_out == su3.TWOROW12 else FLOP_PER_SITE + 4 * 48
 
 
 def slab(n_sites, world, rank):
@@ -398,19 +411,26 @@ def run_native(args, world, rank, local):
     b = gen.bmat(SEED, lattice_id, V_lattice)
     a_dev = a_host.to(dev)
     c_dev = torch.empty_like(a_dev)
+    if (args.dtype != "f64" or args.stride or args.form) and not args.quick:
+        raise SystemExit("--dtype other than f64, --stride and --form time that form alone: use them with --quick")
+    if args.form:  # any form the tuner names; its storage type, arithmetic and stride replace the flags
+        d64, dc = tune.parse_pair(args.form, V)
+        args.dtype = {su3.F64: "f64", su3.F32: "f32", su3.F16: "f16", su3.BF16: "bf16"}[d64.dtype]
+        args.arith = {su3.NATIVE: "native", su3.F32PAIR: "f32pair", su3.HYBRID: "hybrid"}[d64.arith]
+        args.stride = d64.site_stride_bytes
     arith = {"native": su3.NATIVE, "f32pair": su3.F32PAIR, "hybrid": su3.HYBRID}[args.arith]
     dt = {"f64": su3.F64, "f32": su3.F32, "f16": su3.F16, "bf16": su3.BF16}[args.dtype]
-    if (dt != su3.F64 or args.stride) and not args.quick:
-        raise SystemExit("--dtype other than f64 and --stride time that form alone: use them with --quick")
-    d64 = su3.Desc(dt, su3.FULL18, su3.AOS, V, args.stride, arith if dt == su3.F64 else su3.NATIVE)
+    if not args.form:
+        d64 = su3.Desc(dt, su3.FULL18, su3.AOS, V, args.stride, arith if dt == su3.F64 else su3.NATIVE)
+        dc = d64
     a_step, c_step = a_dev, c_dev
-    if dt != su3.F64 or args.stride:
+    if args.form or dt != su3.F64 or args.stride:
         a_step = torch.empty(su3.array_bytes(d64), dtype=torch.uint8, device=dev)
-        c_step = torch.empty_like(a_step)
+        c_step = torch.empty(su3.array_bytes(dc), dtype=torch.uint8, device=dev)
         h.pack(a_dev, d64, a_step, stream)
     if args.launch:
-        h.set_launch_cfg(d64, **parse_launch(args.launch))
-    step = lambda: h.mult(d64, a_step, b, d64, c_step, stream)  # noqa: E731
+        h.set_launch_cfg_for(d64, dc, **parse_launch(args.launch))
+    step = lambda: h.mult(d64, a_step, b, dc, c_step, stream)  # noqa: E731
 
     for _ in range(args.warmup):
         step()
@@ -426,16 +446,18 @@ def run_native(args, world, rank, local):
     h.sync(stream)
     launches = h.launch_count() - n_before
     total_ms = max_over_ranks(total_ms, world, dev)
-    bytes_per_step = float(su3.site_update_bytes(dt)) * V
-    value = sites_all * float(su3.site_update_bytes(dt)) * args.steps / (total_ms * 1e-3) / 1e9
+    site_bytes = float(su3.site_update_bytes(dt, d64.repr, dc.repr))
+    bytes_per_step = site_bytes * V
+    value = sites_all * site_bytes * args.steps / (total_ms * 1e-3) / 1e9
     sups = sites_all * args.steps / (total_ms * 1e-3)
     clocks = clk.summary()
 
     # roofline of the dominant kernel (the FP64 AoS kernel is the whole step); its template's
     # threads per link: 1, or 3 when the launch splits links into rows
-    tpl = 3 if h.get_launch_cfg(d64)["threads_per_link"] == 3 else 1
+    tpl = 3 if h.get_launch_cfg_for(d64, dc)["threads_per_link"] == 3 else 1
     fp64_peak = sms * 2 * 2 * sm_max * 1e6 / 1e12  # 2 DFMA/clk/SM x 2 flop x clock, TFLOP/s
-    achieved_tf = FLOP_PER_SITE * V / (per_launch_ms * 1e-3) / 1e12
+    flop_site = flop_per_site(d64.repr, dc.repr)
+    achieved_tf = flop_site * V / (per_launch_ms * 1e-3) / 1e12
     achieved_gbs = bytes_per_step / (per_launch_ms * 1e-3) / 1e9
     try:  # the FP64 pipe's sustained rate, measured on this device by a diagnostic FMA kernel
         fp64_measured = h.measure_fp64_rate(8192)
@@ -443,6 +465,9 @@ def run_native(args, world, rank, local):
         fp64_measured = None
     pad = ",p%d" % args.stride if args.stride else ""  # padded sites: the kernel of their own
     padded = "true" if args.stride else "false"
+    ops = "%d,%d" % (9 if d64.repr == su3.FULL18 else 6, 3 if dc.repr == su3.FULL18 else 2)  # elements in, rows out
+    if args.form and (d64.repr, dc.repr) != (su3.FULL18, su3.FULL18):
+        pad = ",%s" % args.form  # no traffic record is kept for the two-row forms
     tr = traffic_record().get("su3_aos_kernel<f64,full%s>" % pad, {})
     traffic = None
     if tr and tr.get("source_digest") == source_digest():
@@ -453,11 +478,11 @@ def run_native(args, world, rank, local):
         tr = traffic_record().get("su3_aos_kernel<%s,full%s>" % (args.dtype, pad), {})
         traffic = tr["bytes_per_site"] * V if tr and tr.get("source_digest") == source_digest() else None
         roofline = dict(hbm_roof, bound="hbm", traffic=traffic,
-                        kernel="su3_aos_kernel<NativeOp<%s,9,3>, %d, AOS, %s>" % (args.dtype.upper(), tpl, padded))
+                        kernel="su3_aos_kernel<NativeOp<%s,%s>, %d, AOS, %s>" % (args.dtype.upper(), ops, tpl, padded))
     elif args.arith == "native":
         roofline = {"bound": "alu", "achieved": round(achieved_tf, 4), "peak": round(fp64_peak, 4),
                     "unit": "TFLOP/s", "frac": round(achieved_tf / fp64_peak, 4), "traffic": traffic,
-                    "kernel": "su3_aos_kernel<NativeOp<F64,9,3>, %d, AOS, %s>" % (tpl, padded),
+                    "kernel": "su3_aos_kernel<NativeOp<F64,%s>, %d, AOS, %s>" % (ops, tpl, padded),
                     "peak_source": "FP64 pipe: %d SMs (this device) x 2 DFMA/clk x 2 flop x %.0f MHz (max SM clock)"
                                        % (sms, sm_max),
                     "peak_measured": round(fp64_measured, 4) if fp64_measured else None,
@@ -469,7 +494,7 @@ def run_native(args, world, rank, local):
         tr = traffic_record().get("su3_aos_kernel<f64,full,%s%s>" % (args.arith, pad), {})
         traffic = tr["bytes_per_site"] * V if tr and tr.get("source_digest") == source_digest() else None
         roofline = dict(hbm_roof, bound="hbm", traffic=traffic,
-                        kernel="su3_aos_kernel<%s<9,3>, %d, AOS, %s>" % ("PairF64Op" if args.arith == "f32pair" else "HybridF64Op",
+                        kernel="su3_aos_kernel<%s<%s>, %d, AOS, %s>" % ("PairF64Op" if args.arith == "f32pair" else "HybridF64Op", ops,
                                                                             tpl, padded))
 
     line = {"metric": METRIC, "value": round(value, 2), "unit": "GB/s", "n_gpus": world, "steps": args.steps,
@@ -480,22 +505,23 @@ def run_native(args, world, rank, local):
             "data": "synthetic",
             "config": {"workload": "L=%d %s AoS SU3_Bench link multiply (c[i][j] = a[i][j] x b[j], "
                                    "%d sites, %d B read + %d B written per site)%s%s"
-                                   % (L, args.dtype.upper(), V_lattice, bytes_per_step / V / 2, bytes_per_step / V / 2,
+                                   % (L, args.dtype.upper(), V_lattice, 4 * su3.link_bytes(dt, d64.repr),
+                                      4 * su3.link_bytes(dt, dc.repr),
                                       ", split into %d slabs of contiguous sites" % world if args.shard else "",
                                       ", sites padded to %d B (links only are read and written)" % args.stride
                                       if args.stride else ""),
                        "lattice": "%d^4" % L,
-                       "form": (("f64-full18-aos-" + args.arith) if dt == su3.F64 else args.dtype + "-full18-aos")
-                               + ("-p%d" % args.stride if args.stride else ""),
+                       "form": args.form or ((("f64-full18-aos-" + args.arith) if dt == su3.F64 else args.dtype + "-full18-aos")
+                                             + ("-p%d" % args.stride if args.stride else "")),
                        "seed": SEED,
                        "inputs": "random SU(3) (Gram-Schmidt on Gaussian rows), one lattice per GPU",
                        "l2": "inputs larger than L2 (%.1f GB touched per step vs 129 MB L2): no flush"
                              % (bytes_per_step / 1e9),
-                       "launch_cfg": h.get_launch_cfg(d64), "tuned": bool(tuned) and not args.launch,
+                       "launch_cfg": h.get_launch_cfg_for(d64, dc), "tuned": bool(tuned) and not args.launch,
                        "parallelism": ("slab shards" if args.shard else "replicas") if world > 1 else "single GPU",
                        "sms": sms},
             "site_updates_per_s": round(sups, 1),
-            "gflops": round(FLOP_PER_SITE * sups / 1e9, 2),
+            "gflops": round(flop_site * sups / 1e9, 2),
             "roofline": roofline, "gpu_launches": launches, "clocks": clocks,
             "launch_ms": {"mean": round(per_launch_ms, 4), "median": round(launch_ms[len(launch_ms) // 2], 4),
                           "min": round(launch_ms[0], 4), "max": round(launch_ms[-1], 4)}}

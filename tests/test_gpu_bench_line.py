@@ -45,3 +45,18 @@ def test_shard_mode_line():
     """--shard at N = 1: the one slab is the whole lattice; the line says strong scaling."""
     d = run_bench("--quick", "--shard", "--L", "16", "--steps", "3", "--warmup", "3")
     assert d["scaling"] == "strong" and d["value"] > 0 and d["config"]["parallelism"] == "single GPU"
+
+
+def test_form_and_stride_lines():
+    """--form times any tuner-named form alone (bytes, flops and the kernel's template from its
+    repr pair); --stride times padded sites through the padded kernel."""
+    d = run_bench("--quick", "--L", "16", "--steps", "3", "--warmup", "3", "--form", "f64-2to18-aos-f32pair")
+    assert d["config"]["form"] == "f64-2to18-aos-f32pair" and "384 B read + 576 B written" in d["config"]["workload"]
+    assert d["roofline"]["bound"] == "hbm" and "PairF64Op<6,3>" in d["roofline"]["kernel"]
+    assert d["dtype"].startswith("f32x2") and d["gpu_launches"] == 3
+    d = run_bench("--quick", "--L", "16", "--steps", "3", "--warmup", "3", "--form", "f64-2to18-aos")
+    assert d["roofline"]["bound"] == "alu" and "NativeOp<F64,6,3>" in d["roofline"]["kernel"]
+    assert abs(d["gflops"] / (d["site_updates_per_s"] / 1e9) - 1056) < 0.5
+    d = run_bench("--quick", "--L", "16", "--steps", "3", "--warmup", "3", "--arith", "f32pair", "--stride", "640")
+    assert d["config"]["form"].endswith("-p640") and d["roofline"]["kernel"].endswith("AOS, true>")
+    assert "576 B read + 576 B written" in d["config"]["workload"] and d["value"] > 0
