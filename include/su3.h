@@ -56,7 +56,9 @@ typedef enum { SU3_REPR_FULL18 = 0, SU3_REPR_TWOROW12 = 1 } su3_repr;
  *  AOS:     the paper's Site array (§Background, the Site structure): site i starts at byte
  *           i*site_stride_bytes, link j at +j*link_bytes, element e at +e*2*sizeof(real).
  *           Bytes of a site past its 4 links (the paper's coordinates/index/parity/pad) are
- *           never read by a kernel as data and never written.
+ *           never read by a kernel as data and never written. With a stride wider than the links
+ *           the array moves through 2-D tensor copies (rows = sites) and may hold at most
+ *           2^31 - 1 sites (SU3_ERR_INVALID_ARG beyond).
  *  AOSOA32: blocks of 32 links; element e of link q at complex index
  *           ((q/32)*n_elem + e)*32 + q%32. The last block is padded to 32 links.
  *  SOA:     element e of link q at complex index e*n_links + q.
@@ -105,7 +107,8 @@ typedef struct {
   int32_t block;        /* threads per CTA: a multiple of 32 in [32, 256] */
   int32_t tile_sites;   /* staged: sites per shared-memory tile (1..1024, at most 1 MiB; AOSOA32 a
                            multiple of 8, SOA at most 64; AOS/AOSOA32 tiles are shrunk at launch
-                           until ctas_per_sm CTAs fit in one SM's shared memory);
+                           until ctas_per_sm CTAs fit in one SM's shared memory, and AOS tiles of
+                           padded sites to at most 256, the rows of one tensor copy);
                            AOSOA32/SOA direct loads: links per thread (1, 2 or 4) */
   int32_t stages;       /* staged: shared-memory pipeline depth (2..8); AOSOA32/SOA: 0 = direct */
   int32_t ctas_per_sm;  /* CTAs per SM in the persistent grid (1..32) */
