@@ -60,6 +60,44 @@ LaunchCfg default_cfg(const Form& f) {
   return c;
 }
 
+// cuTensorMapEncodeTiled, reached through the runtime's driver entry point (no link to libcuda).
+using EncodeTiledFn = CUresult (*)(CUtensorMap*, CUtensorMapDataType, cuuint32_t, void*, const cuuint64_t*,
+                                   const cuuint64_t*, const cuuint32_t*, const cuuint32_t*, CUtensorMapInterleave,
+                                   CUtensorMapSwizzle, CUtensorMapL2promotion, CUtensorMapFloatOOBfill);
+
+static EncodeTiledFn encode_tiled() {
+  static const EncodeTiledFn fn = [] {
+    void* f = nullptr;
+    cudaDriverEntryPointQueryResult q = cudaDriverEntryPointSymbolNotFound;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &f, 12000, cudaEnableDefault, &q) != cudaSuccess ||
+        q != cudaDriverEntryPointSuccess)
+      return (EncodeTiledFn) nullptr;
+    return reinterpret_cast<EncodeTiledFn>(f);
+  }();
+  return fn;
+}
+
+su3_status encode_2d(CUtensorMap* m, const void* base, long long inner, long long rows, long long pitch,
+                     long long box_inner, long long box_rows, const LaunchCtx& ctx) {
+  const EncodeTiledFn enc = encode_tiled();
+  if (!enc) {
+    *ctx.err = "cuTensorMapEncodeTiled is not available from the CUDA driver";
+    return SU3_ERR_CUDA;
+  }
+  const cuuint64_t dim[2] = {(cuuint64_t)inner, (cuuint64_t)rows};
+  const cuuint64_t stride[1] = {(cuuint64_t)pitch};
+  const cuuint32_t box[2] = {(cuuint32_t)box_inner, (cuuint32_t)box_rows};
+  const cuuint32_t estride[2] = {1, 1};
+  const CUresult r = enc(m, CU_TENSOR_MAP_DATA_TYPE_UINT64, 2, const_cast<void*>(base), dim, stride, box, estride,
+                         CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
+                         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  if (r != CUDA_SUCCESS) {
+    *ctx.err = "cuTensorMapEncodeTiled failed (error " + std::to_string((int)r) + ")";
+    return SU3_ERR_CUDA;
+  }
+  return SU3_OK;
+}
+
 // AOS arrays whose a or c sites are wider than their links go to the padded kernels.
 static bool padded_sites(const Form& f, long long link_in, long long link_out) {
   return f.layout == SU3_LAYOUT_AOS && (f.a_stride != 4 * link_in || f.c_stride != 4 * link_out);

@@ -56,12 +56,14 @@ struct AosArgs {
   unsigned* status;
   int a_padded;       // AOS: a's sites are wider than their links; tiles arrive through SiteMaps::a
   int c_padded;       // AOS: c's sites are wider than their links; tiles leave through SiteMaps::c
+  int soa_tensor;     // SOA: a tile's element planes move as one 2-D tensor copy each way
   BMat<A> b;
 };
 
-// Tensor maps of padded AOS arrays (rows = sites, a row = the site's links as 8-byte elements,
-// a box = tile_sites rows). A kernel parameter of their own: the copies take their address, and
-// the other arguments stay plain constants.
+// Tensor maps of a and c for the TMA engine: padded AOS arrays (rows = sites, a row = the site's
+// links as 8-byte elements, a box = tile_sites rows), or SOA arrays (rows = element planes, a box
+// = the 256 links of one tile in every plane). A kernel parameter of their own: the copies take
+// their address, and the other arguments stay plain constants.
 struct SiteMaps {
   CUtensorMap a;
   CUtensorMap c;
@@ -163,6 +165,13 @@ __global__ void __launch_bounds__(256) su3_aos_kernel(const __grid_constant__ Ao
       mbar_arrive_expect_tx(&full[s], bytes);
       bulk_g2s(dst, p.a + 4 * first * kLinkIn, bytes, &full[s], pol);
     } else {
+      if (p.soa_tensor) {
+        // the tile's 256 links of every element plane in one 2-D tensor copy (links past the
+        // array arrive as zeros and count); x in 8-byte elements
+        mbar_arrive_expect_tx(&full[s], (unsigned)(NE_IN * kSoaPlaneLinks * kVec));
+        tma_load_2d(dst, &maps.a, (int)(4 * first * kVec / 8), 0, &full[s], pol);
+        return;
+      }
       const unsigned plane = (unsigned)(4 * nt * kVec);
       mbar_arrive_expect_tx(&full[s], plane * NE_IN);
 #pragma unroll 1
@@ -278,6 +287,8 @@ __global__ void __launch_bounds__(256) su3_aos_kernel(const __grid_constant__ Ao
           const size_t off = ((size_t)whole * NE_OUT * 32 + (size_t)tid * 32) * kVec;
           bulk_s2g(cblk + off, out + off, (unsigned)(rem * kVec), pol);
         }
+      } else if (p.soa_tensor) {  // every element plane in one tensor copy (links past the array are not written)
+        if (tid == 0) tma_store_2d(&maps.c, (int)(4 * first * kVec / 8), 0, out, pol);
       } else {
         if (tid < NE_OUT)
           bulk_s2g(p.c + ((long long)tid * p.n_links + 4 * first) * kVec, out + (size_t)tid * kSoaPlaneLinks * kVec,
@@ -365,9 +376,18 @@ inline su3_status cuda_fail(const LaunchCtx& ctx, const char* what, cudaError_t 
 // Max rows (sites) of one tensor-copy box.
 constexpr long long kMaxBoxRows = 256;
 
-// Encodes the tensor map of an AOS array of padded sites (defined with the padded kernels).
-su3_status encode_sites(CUtensorMap* m, const void* base, long long n_sites, long long stride, long long row_bytes,
-                        long long rows, const LaunchCtx& ctx);
+// A 2-D tensor map for the TMA engine over 8-byte elements: `rows` rows of `inner` elements,
+// `pitch` bytes apart (a multiple of 16); a box is box_rows rows of box_inner elements.
+su3_status encode_2d(CUtensorMap* m, const void* base, long long inner, long long rows, long long pitch,
+                     long long box_inner, long long box_rows, const LaunchCtx& ctx);
+
+// An AOS array of padded sites: n_sites rows `stride` bytes apart, each row the site's row_bytes
+// of links (the bytes after the links lie outside the tensor, so no copy reads or writes them); a
+// box is `rows` whole rows.
+inline su3_status encode_sites(CUtensorMap* m, const void* base, long long n_sites, long long stride,
+                               long long row_bytes, long long rows, const LaunchCtx& ctx) {
+  return encode_2d(m, base, row_bytes / 8, n_sites, stride, row_bytes / 8, rows, ctx);
+}
 
 // The same dispatch over forms, instantiated once per kind of site stride (each in its own
 // translation unit, so that they compile in parallel).
@@ -488,7 +508,16 @@ static su3_status run_aos(const Form& f, const LaunchCfg& cfg, const void* a, co
     return SU3_OK;
   };
   SiteMaps maps;
-  memset(&maps, 0, sizeof(maps));  // not read by the packed kernels
+  memset(&maps, 0, sizeof(maps));  // read by the padded kernels and the SOA tensor copies only
+  // SOA tiles of exactly 256 links whose plane rows fit one box (at most 256 8-byte elements, so
+  // 4- and 8-byte complex elements) move as one tensor copy each way
+  p.soa_tensor = LAYOUT == SU3_LAYOUT_SOA && ts == kSoaPlaneLinks / 4 && kVec <= 8 ? 1 : 0;
+  if (p.soa_tensor) {
+    const long long row = p.n_links * kVec;  // one element plane, bytes (a multiple of 16)
+    su3_status st = encode_2d(&maps.a, a, row / 8, Op::kNeIn, row, kSoaPlaneLinks * kVec / 8, Op::kNeIn, ctx);
+    if (st == SU3_OK) st = encode_2d(&maps.c, c, row / 8, Op::kNeOut, row, kSoaPlaneLinks * kVec / 8, Op::kNeOut, ctx);
+    if (st != SU3_OK) return st;
+  }
   if constexpr (PADDED) {
     if (a_pad) {
       const su3_status st = encode_sites(&maps.a, a, f.n_sites, f.a_stride, 4 * kLinkIn, ts, ctx);
