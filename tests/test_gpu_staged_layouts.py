@@ -1,6 +1,8 @@
 """The element-major layouts (AOSOA32, SOA) through the staged kernel: tiles moved between HBM and
-shared memory by bulk copies (whole 32-link blocks for AOSOA32, one copy per element plane for
-SOA), computed in place with the element stride of the layout, and stored back the same way.
+shared memory by bulk copies (whole 32-link blocks for AOSOA32; for SOA one 2-D tensor copy of
+every element plane's 256 links when a tile is 64 sites of 4- or 8-byte elements, one copy per
+element plane otherwise; V = 1 puts a whole array inside one box), computed in place with the
+element stride of the layout, and stored back the same way.
 
 Every form against the oracle and bit for bit against the direct-load kernel (both run the same
 per-link operations in the same order), ragged sizes whose last AOSOA32 block is partial, the row
