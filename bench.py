@@ -359,14 +359,40 @@ def traffic_record():
 AOS_KERNEL_SOURCES = ("su3_device.cuh", "su3_internal.h", "su3_stream.cuh", "su3_stream.cu", "su3_stream_padded.cu")
 
 
+def code_only(text):
+    """C/C++/CUDA source with comments removed and whitespace runs collapsed (string and character
+    literals kept as they are), so that editing a comment leaves the digest alone."""
+    out, i, n = [], 0, len(text)
+    while i < n:
+        c = text[i]
+        if c in "\"'":  # a literal: copy it through its closing quote, honouring escapes
+            j = i + 1
+            while j < n and text[j] != c:
+                j += 2 if text[j] == "\\" else 1
+            out.append(text[i:j + 1])
+            i = j + 1
+        elif text.startswith("//", i):
+            i = text.find("\n", i)
+            i = n if i < 0 else i
+        elif text.startswith("/*", i):
+            j = text.find("*/", i + 2)
+            i = n if j < 0 else j + 2
+            out.append(" ")
+        else:
+            out.append(c)
+            i += 1
+    return " ".join("".join(out).split())
+
+
 def source_digest():
-    """Digest of the AoS kernels' sources: a traffic record taken under another digest is stale."""
+    """Digest of the AoS kernels' code (comments and layout ignored): a traffic record taken under
+    another digest is stale."""
     import hashlib
     d = hashlib.sha256()
     csrc = os.path.join(ROOT, "paper_2103_00571_gb300", "csrc")
     for n in AOS_KERNEL_SOURCES:
-        with open(os.path.join(csrc, n), "rb") as f:
-            d.update(n.encode() + f.read())
+        with open(os.path.join(csrc, n), encoding="utf-8") as f:
+            d.update((n + "\n" + code_only(f.read())).encode())
     return d.hexdigest()[:16]
 
 

@@ -9,8 +9,9 @@
 //  * The staged kernel (every layout): a persistent CTA streams tiles of `tile_sites` sites through
 //    a `stages`-deep ring of shared-memory buffers. Each tile arrives by bulk copies completing on
 //    one mbarrier: one copy of whole sites (AOS; padded sites: one 2-D tensor copy of the tile's
-//    links), one copy of whole 32-link blocks (AOSOA32), or one copy per element plane into a
-//    plane slot of 256 links (SOA). Each thread multiplies work
+//    links), one copy of whole 32-link blocks (AOSOA32), or the element planes into plane slots
+//    of 256 links (SOA: one 2-D tensor copy of all planes for 64-site tiles of 4- or 8-byte
+//    elements, one copy per plane otherwise). Each thread multiplies work
 //    items q = tid, tid+block, ... of the tile: whole links, or single output rows when
 //    threads_per_link is 3, and writes the result back in place (two-row in, full out: into a
 //    3-deep ring of output buffers in the same layout). Warp 0 then bulk-stores the tile and

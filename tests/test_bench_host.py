@@ -110,3 +110,13 @@ def test_summary_ends_the_line_and_stays_short():
     assert s["site640_Gsite_per_s"] == {"native": 1.38, "f32pair": 5.09}
     assert s["e2e"]["GBps"] == 333.1 and s["batched"]["graph_persistent"][2] is True
     assert len(json.dumps({"summary": s})) < 1400
+
+
+def test_digest_ignores_comments_only():
+    """The traffic records' digest follows the code: comments and layout do not change it, while a
+    change in code, string literals included, does."""
+    base = 'int a = 1; // x\n/* y */ const char* s = "// kept"; char q = \'"\';\n'
+    assert bench.code_only(base) == bench.code_only(base.replace("// x", "// other words").replace("/* y */", "\n\n"))
+    assert bench.code_only(base) != bench.code_only(base.replace("a = 1", "a = 2"))
+    assert bench.code_only(base) != bench.code_only(base.replace("// kept", "// changed"))
+    assert "// kept" in bench.code_only(base) and "x" not in bench.code_only(base).replace("// kept", "")
