@@ -49,41 +49,52 @@ def L48():
     return a, b, oracle.mult(a, b)
 
 
-@pytest.mark.parametrize("dtype,arith,rep,layout", [
-    (su3.F64, su3.NATIVE, su3.FULL18, su3.AOS), (su3.F64, su3.F32PAIR, su3.FULL18, su3.AOS),
-    (su3.F16, su3.NATIVE, su3.FULL18, su3.AOS), (su3.BF16, su3.NATIVE, su3.FULL18, su3.AOS),
-    (su3.F32, su3.NATIVE, su3.FULL18, su3.AOS), (su3.F64, su3.NATIVE, su3.FULL18, su3.SOA),
-    (su3.F64, su3.F32PAIR, su3.FULL18, su3.AOSOA32), (su3.F16, su3.NATIVE, su3.FULL18, su3.AOSOA32),
-    (su3.F64, su3.F32PAIR, su3.TWOROW12, su3.AOS), (su3.F32, su3.NATIVE, su3.TWOROW12, su3.AOS)],
-    ids=["f64", "f64-f32pair", "f16", "bf16", "f32", "f64-soa", "f64-f32pair-aosoa32", "f16-aosoa32",
-         "f64-f32pair-2row", "f32-2row"])
-def test_L64_sampled(h, dtype, arith, rep, layout):
-    """L=64 (16.7M sites, every array past 2^32 bytes for FP64): the whole lattice runs on the GPU;
-    65,536 random sites are recomputed by the oracle from the same generator and compared element
-    by element."""
+F64, F32, F16, BF16 = su3.F64, su3.F32, su3.F16, su3.BF16
+NAT, PAIR, FULL, TWO = su3.NATIVE, su3.F32PAIR, su3.FULL18, su3.TWOROW12
+AOS, SOA, AOSOA = su3.AOS, su3.SOA, su3.AOSOA32
+
+
+@pytest.mark.parametrize("dtype,arith,rep,rep_out,layout,stride", [
+    (F64, NAT, FULL, FULL, AOS, 0), (F64, PAIR, FULL, FULL, AOS, 0), (F16, NAT, FULL, FULL, AOS, 0),
+    (BF16, NAT, FULL, FULL, AOS, 0), (F32, NAT, FULL, FULL, AOS, 0), (F64, NAT, FULL, FULL, SOA, 0),
+    (F16, NAT, FULL, FULL, SOA, 0), (F32, NAT, FULL, FULL, SOA, 0),
+    (F64, PAIR, FULL, FULL, AOSOA, 0), (F16, NAT, FULL, FULL, AOSOA, 0), (F64, PAIR, TWO, TWO, AOS, 0),
+    (F32, NAT, TWO, TWO, AOS, 0), (F64, PAIR, TWO, FULL, AOS, 0), (F64, NAT, TWO, FULL, AOS, 0),
+    (F64, NAT, FULL, FULL, AOS, 640), (F64, PAIR, FULL, FULL, AOS, 640)],
+    ids=["f64", "f64-f32pair", "f16", "bf16", "f32", "f64-soa", "f16-soa", "f32-soa", "f64-f32pair-aosoa32",
+         "f16-aosoa32", "f64-f32pair-2row", "f32-2row", "f64-f32pair-2row-to-full", "f64-2row-to-full",
+         "f64-site640", "f64-f32pair-site640"])
+def test_L64_sampled(h, dtype, arith, rep, rep_out, layout, stride):
+    """L=64 (16.7M sites, every array past 2^32 bytes for FP64): the whole lattice runs on the GPU
+    in the tuned launch configuration (SoA tiles through tensor copies, two-row in / full out
+    through per-warp output copies, the paper's 640-byte sites through the padded kernel); 65,536
+    random sites are recomputed by the oracle from the same generator and compared element by
+    element."""
     import torch
     V = 64 ** 4
     a = gen.sites(gen.DEFAULT_SEED, 0, V)
     b = gen.bmat(gen.DEFAULT_SEED, 0, V)
     a_dev = torch.from_numpy(a).cuda()
     del a
-    d = su3.Desc(dtype, rep, layout, V, 0, arith)
-    if dtype == su3.F64 and rep == su3.FULL18 and layout == su3.AOS:
+    d = su3.Desc(dtype, rep, layout, V, stride, arith)
+    dc = su3.Desc(dtype, rep_out, layout, V, stride, arith)
+    if dtype == su3.F64 and rep == su3.FULL18 and layout == su3.AOS and not stride:
         abuf = a_dev
     else:
         abuf = torch.empty(su3.array_bytes(d), dtype=torch.uint8, device="cuda")
         h.pack(a_dev, d, abuf)
-    cbuf = torch.empty(su3.array_bytes(d), dtype=torch.uint8, device="cuda")
-    h.mult(d, abuf, b, d, cbuf)
+    cbuf = torch.empty(su3.array_bytes(dc), dtype=torch.uint8, device="cuda")
+    h.mult(d, abuf, b, dc, cbuf)
     out = a_dev if abuf is not a_dev else torch.empty_like(a_dev)
-    h.unpack(d, cbuf, out)
+    h.unpack(dc, cbuf, out)
     h.sync()
+    del abuf, cbuf
     idx = np.sort(np.random.default_rng(64).choice(V, 65536, replace=False))
     idx[0], idx[-1] = 0, V - 1  # both ends of the lattice
     got = out.view(V, 72)[torch.from_numpy(idx).cuda()].cpu().numpy()
     ref = oracle.mult_sites(gen.sites_at(gen.DEFAULT_SEED, 0, idx), b)
     mx, rms = oracle.error(got, ref)
-    assert mx <= tol(dtype, rep), (mx, rms)
+    assert mx <= tol(dtype, rep, rep_out), (mx, rms)
 
 
 @pytest.mark.parametrize("arith", [su3.NATIVE, su3.F32PAIR], ids=["native", "f32pair"])
@@ -118,3 +129,7 @@ def test_every_bench_form_under_tuned_configs(h):
         got = run_form(h, a, b, dt, ri, ro, lay, arith=ar[0] if ar else su3.NATIVE)
         mx, _ = oracle.error(got, ref)
         assert mx <= tol(dt, ri, ro), (name, mx)
+    for arith in (su3.NATIVE, su3.F32PAIR):  # the paper's 640-byte Site (bench.py's paper_site640 leg)
+        got = run_form(h, a, b, su3.F64, stride=640, arith=arith)
+        mx, _ = oracle.error(got, ref)
+        assert mx <= 1e-13, ("site640", arith, mx)
