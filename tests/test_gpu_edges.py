@@ -167,6 +167,30 @@ def test_mixed_site_strides_bitwise(arith, reprs):
     h.close()
 
 
+@pytest.mark.parametrize("arith", [su3.NATIVE, su3.F32PAIR])
+@pytest.mark.parametrize("V", [1, 7, 65])
+def test_padded_arrays_smaller_than_a_tile(h, arith, V):
+    """Padded sites fewer than one tile's rows: the tensor copy's box reaches past the array (rows
+    there arrive as zeros and are never stored), and the bytes after each site's links stay."""
+    import torch
+    a, b = gen.lattice(16, V)
+    d = su3.Desc(su3.F64, su3.FULL18, su3.AOS, V, 640, arith)
+    saved = h.get_launch_cfg(d)
+    try:
+        h.set_launch_cfg(d, block=256, tile_sites=64, stages=3, ctas_per_sm=2, threads_per_link=1)
+        abuf = torch.full((V * 640,), 0x3C, dtype=torch.uint8, device="cuda")
+        h.pack(to_dev(a), d, abuf)
+        cbuf = torch.full_like(abuf, 0xC3)
+        h.mult(d, abuf, b, d, cbuf)
+        h.sync()
+    finally:
+        h.set_launch_cfg(d, **saved)
+    host = cbuf.view(V, 640).cpu()
+    assert bool(torch.all(host[:, 576:] == 0xC3)), "bytes after the links were written"
+    got = host[:, :576].contiguous().view(torch.float64).numpy().reshape(-1)
+    assert oracle.error(got, oracle.mult(a, b))[0] <= 1e-13
+
+
 def test_canaries_packed(h):
     import torch
     V = 1237
