@@ -148,7 +148,9 @@ su3_status su3_finalize(su3_handle* h);
  * (rows 0-1 of c only), TWOROW12 -> FULL18 (row 2 of a rebuilt in registers).
  * a_dev == c_dev (exactly in place, same desc) is allowed; any other overlap is INVALID_ARG.
  * For F16/BF16/F32 storage, b is rounded once to FP32; results are rounded once to storage.
- * Asynchronous on `stream`.
+ * Asynchronous on `stream`: the call only enqueues work there (b travels by value in the launch
+ * parameters), so it can be captured into a CUDA graph on a capturing stream and replayed, with the
+ * eager call's bits (tested); make one eager call of the same form first, outside the capture.
  */
 su3_status su3_mult(su3_handle* h, const su3_desc* a_desc, const void* a_dev,
                     const double* b, const su3_desc* c_desc, void* c_dev, void* stream);
