@@ -94,9 +94,8 @@ __device__ __forceinline__ int tile_link_base(int q) {
 // Tiles: AOS any number of sites; AOSOA32 a multiple of 8 sites (whole 32-link blocks; the last
 // block of an array is padded, so it is always read whole); SOA at most 64 sites (256 links).
 // PADDED (AOS only): a's or c's sites are wider than their links, and `maps` holds their tensor
-// maps; otherwise `maps` is not read. (A kernel of its own per PADDED rather than one body shared
-// through a device function: reading the __grid_constant__ arguments through a reference measured
-// up to 11 % slower on the narrow forms.)
+// maps; otherwise `maps` is read only by SOA tensor copies. One instantiation per PADDED value, so
+// the packed kernels keep their own code.
 template <class Op, int TPL, int LAYOUT, bool PADDED>
 __global__ void __launch_bounds__(256) su3_aos_kernel(const __grid_constant__ AosArgs<typename Op::BArg> p,
                                                       const __grid_constant__ SiteMaps maps) {
@@ -187,9 +186,9 @@ __global__ void __launch_bounds__(256) su3_aos_kernel(const __grid_constant__ Ao
     for (int k = 0; k < prefetch && k < my_tiles; ++k) issue_load(k);
 
   // packed kernel: one copy of a whole tile of c. Its per-site branch below (a c stride wider
-  // than the tile's) serves no launch, since padded strides take the PADDED kernel, but the
-  // kernel without it measured 5-11 % slower on the narrow (FP32/FP16/BF16) forms, a
-  // code-generation effect, so it stays.
+  // than the tile's) serves no launch, since padded strides take the PADDED kernel, but two
+  // variants of the kernel without it measured 5-11 % slower on the narrow (FP32/FP16/BF16)
+  // forms, a code-generation effect, so it stays.
   const bool packed_store = kInPlace ? (p.a_stride == 4 * kLinkIn && p.c_stride == 4 * kLinkOut)
                                      : (p.c_stride == 4 * kLinkOut);
   int issued = my_tiles < prefetch ? my_tiles : prefetch;  // loads issued so far (thread 0's view)
