@@ -133,3 +133,36 @@ def test_every_bench_form_under_tuned_configs(h):
         got = run_form(h, a, b, su3.F64, stride=640, arith=arith)
         mx, _ = oracle.error(got, ref)
         assert mx <= 1e-13, ("site640", arith, mx)
+
+
+@pytest.mark.parametrize("arith", [su3.NATIVE, su3.F32PAIR], ids=["native", "f32pair"])
+def test_L64_adjacent_sampled(h, arith):
+    """The adjacent products bench.py times at L=64 (a b^dagger, a^dagger b, a v, a^dagger v) on the
+    whole FP64 lattice in HBM, compared with the oracle on 65,536 sampled sites."""
+    import torch
+    V = 64 ** 4
+    a = gen.sites(gen.DEFAULT_SEED, 0, V)
+    b = gen.bmat(gen.DEFAULT_SEED, 0, V)
+    a_dev = torch.from_numpy(a).cuda()
+    del a
+    d = su3.Desc(su3.F64, su3.FULL18, su3.AOS, V, 0, arith)
+    idx = np.sort(np.random.default_rng(65).choice(V, 65536, replace=False))
+    idx[0], idx[-1] = 0, V - 1
+    sel = torch.from_numpy(idx).cuda()
+    a_sel = gen.sites_at(gen.DEFAULT_SEED, 0, idx)
+    c = torch.empty_like(a_dev)
+    for op, ref in ((su3.OP_NA, oracle.mult_na), (su3.OP_AN, oracle.mult_an)):
+        c.fill_(float("nan"))
+        h.mult_op(op, d, a_dev, b, d, c)
+        h.sync()
+        got = c.view(V, 72)[sel].cpu().numpy()
+        assert oracle.error(got, ref(a_sel, b))[0] <= 1e-13, op
+    del c
+    v = np.random.default_rng(64).standard_normal(24) / 2.0
+    w = torch.empty(V * 24, dtype=torch.float64, device="cuda")
+    for adjoint in (False, True):
+        w.fill_(float("nan"))
+        h.mat_vec(d, a_dev, v, w, adjoint=adjoint)
+        h.sync()
+        got = w.view(V, 24)[sel].cpu().numpy()
+        assert oracle.error(got, oracle.mat_vec(a_sel, v, adjoint=adjoint))[0] <= 1e-13, adjoint
