@@ -617,7 +617,8 @@ def summary(line):
                           if n in bt}
     e2e = line.get("e2e")
     if e2e:
-        out["e2e"] = {"GBps": e2e["value"], "path": e2e.get("path"), "vs_copies_only": e2e.get("vs_copies_only")}
+        out["e2e"] = {"GBps": e2e["value"], "path": e2e.get("path"), "vs_copies_only": e2e.get("vs_copies_only"),
+                      "matches_device_step": e2e.get("matches_device_step")}
     cpu = line.get("cpu_baseline")
     if cpu:
         out["cpu_oracle_GBps"] = cpu["value"]
@@ -824,6 +825,14 @@ def e2e_leg(h, torch, su3, a_host, b, V, args, stream, world, dev, a_dev=None, c
         cel = max_over_ranks(cel, world, dev)
         out["copies_only_GBps"] = round(1152.0 * sites_all * k / cel / 1e9, 2)
         out["vs_copies_only"] = round(gbs / out["copies_only_GBps"], 3)
+    if c_dev is not None and args.arith == "native":
+        # the timed path's result (the copies above reused c_host, so it is computed once more) on
+        # 65,536 sampled sites, bit for bit against the device-resident step's c (same arithmetic)
+        h.mult_host(d64, a_host.data_ptr(), b, d64, c_host.data_ptr(), stream)
+        idx = np.sort(np.random.default_rng(1).choice(V, min(V, 65536), replace=False))
+        got = c_host.view(V, 72)[torch.from_numpy(idx)].numpy()
+        want = c_dev.view(V, 72)[torch.from_numpy(idx).to(c_dev.device)].cpu().numpy()
+        out["matches_device_step"] = bool(np.array_equal(got, want))
     # for context: the same calls forced through the staged (chunked copy) path
     h.set_host_path(su3.HOST_STAGED)
     try:
