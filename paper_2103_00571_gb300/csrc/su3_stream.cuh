@@ -400,8 +400,9 @@ su3_status launch_adjacent_padded(int which, const Form& f, const LaunchCfg& cfg
 // a multiple of 8 (whole 32-link blocks); SOA at most 64 sites, each element plane in a slot of
 // 256 links, so an SOA stage is NE x 256 storage vectors whatever tile_sites is.
 template <class Op, int LAYOUT, bool PADDED>
-static su3_status run_aos(const Form& f, const LaunchCfg& cfg, const void* a, const double* b, void* c,
+static su3_status run_aos(const Form& f, const LaunchCfg& cfg_in, const void* a, const double* b, void* c,
                           const LaunchCtx& ctx) {
+  LaunchCfg cfg = cfg_in;  // the launch may narrow its block for a small array (below)
   using BA = typename Op::BArg;
   using V = typename Op::V;
   constexpr bool kInPlace = (Op::kNeOut == Op::kNeIn);
@@ -461,6 +462,18 @@ static su3_status run_aos(const Form& f, const LaunchCfg& cfg, const void* a, co
         while (ts > quantum && smem_of(ts) > per_cta) ts -= quantum;
         if (ts >= 8) ts &= ~7LL;
       }
+    }
+  }
+  // an array with fewer tiles than SMs: narrower tiles, in CTAs just wide enough for them, spread
+  // it over more SMs, so that its warps do not queue on a few SMs' pipes (every launch shape gives
+  // the same bits; this only shortens small launches)
+  if (f.n_sites > 0 && (f.n_sites + ts - 1) / ts < ctx.num_sms) {
+    long long t2 = (f.n_sites + ctx.num_sms - 1) / ctx.num_sms;
+    t2 = std::max(quantum, (t2 + quantum - 1) / quantum * quantum);
+    if (t2 < ts) {
+      ts = t2;
+      const long long items = ts * 4 * (cfg.threads_per_link == 1 ? 1 : (Op::kRowSplit ? Op::kNeOut / 3 : 1));
+      cfg.block = (int)std::min<long long>(cfg.block, std::max<long long>(32, (items + 31) / 32 * 32));
     }
   }
   AosArgs<BA> p;
